@@ -1,0 +1,392 @@
+"""Throughput of the truncated-solver loop pipeline on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one batch of Z4 sources:
+  nrhs low-precision bulk sources (multi-RHS CG on M^dag M, 16-bit sloppy)
+  + n_hp correction sources (FP32/FP64-reliable CG and the same LP map)
+  + the one-end contraction of all of them over 160 insertions and the
+    p^2 <= 9 momenta, FP64 accumulation and the TSM combination.
+metric: TSM sources/s (all sources of the step, LP and HP) at 24^3 x 48.
+
+  value  -- device-timed (CUDA events) tsm_solve_tsm_dev: result stays in HBM
+  e2e    -- wall time of tsm_solve_tsm with the result read back to pinned host
+            memory and the momentum list sent every step
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "workload": "tsm_loops_24x24x24x48",
+    "dims": [24, 24, 24, 48],
+    "eps": 0.25, "gauge_seed": 3, "kappa": 0.125, "mu": 0.005, "t_bc": -1,
+    "rho_lp": 1e-2, "rho_hp": 1e-8, "p2max": 9, "n_insertions": 160,
+}
+METRIC = "TSM sources/s incl. 160-insertion loops, 24^3x48"
+UNIT = "sources/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=32)
+    ap.add_argument("--n-hp", type=int, default=2)
+    ap.add_argument("--lp", default="f16", choices=["f16", "bf16"])
+    ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,T (default 24,24,24,48)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(dims, kappa, mu, lp_iters, n_mom_all, budget_s=20.0):
+    """The oracle as it stands, on a bounded sample of one source at full size.
+
+    Sample: oracle M^dag M applications (its CG inner step) and the oracle's
+    densities of a subset of insertions plus their direct projection, each
+    timed; one source's cost = lp_iters x t(M^dag M) + 160/n x t(densities and
+    projection of n insertions).  lp_iters is the mean LP iteration count of
+    the GPU run (the oracle's FP64 CG needs at least as many).
+    """
+    import numpy as np
+    from oracle import contract, dirac, lattice, momenta, philox
+    from paper_1401_6750_gb300 import synth
+    t0 = time.time()
+    links = synth.gauge_links(dims, 0.25, 3)
+    u = lattice.effective_links(links, -1)
+    eta = philox.z4_source(dims, 1003, 0)
+    t1 = time.time()
+    n_app = 0
+    x = eta
+    while True:
+        x = dirac.apply_MdagM(u, x, kappa, mu)
+        n_app += 1
+        if time.time() - t1 > budget_s / 3 or n_app >= 4:
+            break
+    t_mdm = (time.time() - t1) / n_app
+    # densities of the 16 ultra-local insertions of one flavour + projection
+    moms = momenta.momentum_list(9)
+    t2 = time.time()
+    phi = dirac.gamma5(eta)
+    from oracle.gamma import INSERTIONS
+    dens = np.stack([contract.bilinear(phi, INSERTIONS[gi], eta) for gi in range(16)])
+    contract.project(dens, dims, moms)
+    t_ins = (time.time() - t2) / 16
+    per_source = lp_iters * t_mdm + 160 * t_ins * 1.0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {
+        "value": 1.0 / per_source, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "sample": ("oracle numpy FP64 at %s: %d M^dag M applications (%.2f s each) x %.0f LP iterations"
+                   " + 16 ultra-local insertion densities with direct p^2<=9 projection (%.2f s per insertion)"
+                   " x 160; setup %.1f s excluded" % ("x".join(map(str, dims)), n_app, t_mdm, lp_iters, t_ins,
+                                                       t1 - t0)),
+    }
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle, timed on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    dims = [int(v) for v in args.dims.split(",")] if args.dims else WORKLOAD["dims"]
+    vals = []
+    for k in range(args.warmup + args.steps):
+        b = cpu_baseline(dims, WORKLOAD["kappa"], WORKLOAD["mu"], lp_iters=60.0, n_mom_all=123,
+                         budget_s=15.0)
+        if k >= args.warmup:
+            vals.append(b)
+    v = sorted(x["value"] for x in vals)[len(vals) // 2]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, dims=dims),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                         "sample": vals[0]["sample"] + "; LP iteration count fixed at 60 (not measured here)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _dslash_roofline(g, abi, torch, peak, prec, nrhs, reps=10):
+    """Stand-alone operator M (tsm_dslash_tm) with an L2 flush before each
+    launch; each launch is bracketed by CUDA events on the launching stream."""
+    import ctypes
+    dims = g.dims
+    v = g.volume
+    stream = torch.cuda.current_stream()
+    src = g.sources(77, 0, nrhs, prec)
+    out = g.empty_native(prec, nrhs)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    link_b = {abi.TSM_F16: 96, abi.TSM_BF16: 96, abi.TSM_F32: 192, abi.TSM_F64: 576}[prec]
+    spin_b = 16 * abi.CHUNKS[prec]
+    times = []
+    for k in range(reps + 2):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        abi.check(abi.lib().tsm_dslash_tm(g.handle, 0.125, 0.005, abi.TSM_OP_M, prec, ctypes.c_void_p(src.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), nrhs,
+                                          ctypes.c_void_p(stream.cuda_stream)), "tsm_dslash_tm")
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 2:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    t = sorted(times)[len(times) // 2]
+    bytes_ = v * (link_b + nrhs * 2 * spin_b)
+    return {"kernel": "dslash_tm M %s r12, %d rhs, %s" % ({2: "f16", 3: "bf16", 1: "f32", 0: "f64"}[prec], nrhs,
+                                                          "x".join(map(str, dims))),
+            "achieved": bytes_ / t / 1e9, "peak": peak, "unit": "GB/s", "frac": bytes_ / t / 1e9 / peak,
+            "bytes_per_launch": bytes_, "us_per_launch": t * 1e6, "l2": "flushed (512 MB write) before each launch"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1401_6750_gb300 import abi, api, build, synth
+    build.build()
+    lib = abi.lib()
+    # one dedicated stream: the library launches on it and the events are recorded on it
+    bench_stream = torch.cuda.Stream()
+    torch.cuda.set_stream(bench_stream)
+
+    dims = [int(v) for v in args.dims.split(",")] if args.dims else WORKLOAD["dims"]
+    w = dict(WORKLOAD, dims=dims)
+    links = synth.gauge_links(dims, w["eps"], w["gauge_seed"])
+    ctx = api.Context(local)
+    g = api.Gauge(ctx, links, dims, w["t_bc"], precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16, abi.TSM_BF16))
+    del links
+    lp_solver = abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16
+    moms = np.ascontiguousarray(np.array(api.momentum_table(w["p2max"]), dtype=np.int32))
+    n_mom = moms.shape[0]
+    T = dims[3]
+    n_out = 160 * n_mom * T * 2
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    out_dev = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    host_out = torch.empty(n_out, dtype=torch.float64, pin_memory=True)
+    units_per_step = args.nrhs + args.n_hp
+
+    def params(step):
+        # distinct sources every step and on every rank (weak scaling over replicas)
+        seed = 1003 + 1000003 * rank + 7919 * step
+        return abi.tsm_params(w["kappa"], w["mu"], args.nrhs, args.n_hp, w["rho_lp"], w["rho_hp"], lp_solver,
+                              abi.TSM_SOLVER_F32_RELIABLE, seed, 20000, args.nrhs, n_mom,
+                              moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+
+    stats_log = []
+
+    def step_dev(k):
+        p = params(k)
+        st = abi.tsm_stats()
+        rc = lib.tsm_solve_tsm_dev(g.handle, ctypes.byref(p), ctypes.c_void_p(out_dev.data_ptr()), None,
+                                   ctypes.byref(st), sp)
+        abi.check(rc, "tsm_solve_tsm_dev")
+        stats_log.append({f: getattr(st, f) for f, _ in st._fields_})
+
+    def step_host(k):
+        p = params(k)
+        rc = lib.tsm_solve_tsm(g.handle, ctypes.byref(p), ctypes.c_void_p(host_out.data_ptr()), None, None, sp)
+        abi.check(rc, "tsm_solve_tsm")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for k in range(args.warmup):
+        step_dev(k)
+    launches0 = lib.tsm_kernel_launches()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        step_dev(args.warmup + k)
+    e1.record(stream)
+    e1.synchronize()
+    elapsed = e0.elapsed_time(e1) * 1e-3
+    clk = clocks.stop()
+    launches = lib.tsm_kernel_launches() - launches0
+    barrier()
+    elapsed = max_over_ranks(elapsed)
+    value = world * units_per_step * args.steps / elapsed
+    timed_stats = stats_log[args.warmup:]
+    lp_iters = sum(s["lp_iterations_total"] for s in timed_stats) / max(1, sum(
+        (args.nrhs + args.n_hp) for _ in timed_stats))
+    hp_iters = sum(s["hp_iterations_total"] for s in timed_stats) / max(1, args.n_hp * len(timed_stats))
+
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            step_host(args.warmup + args.steps + k)
+        torch.cuda.synchronize()
+        t_e2e = max_over_ranks(time.perf_counter() - t0)
+        n_contract_calls = 1 + 2 * ((args.n_hp + args.nrhs - 1) // args.nrhs) if args.n_hp else 1
+        e2e = {"value": world * units_per_step * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(n_contract_calls * moms.nbytes + ctypes.sizeof(abi.tsm_params)),
+               "d2h_bytes_per_step": int(n_out * 8)}
+
+    # roofline: one profiled step (kernel classes event-timed), plus the stand-alone operator
+    peak, peak_kind = measured_peak_gbs()
+    barrier()
+    lib.tsm_profile_enable(1)
+    step_dev(10**6)
+    torch.cuda.synchronize()
+    lib.tsm_profile_enable(0)
+    n = lib.tsm_profile_read(None, 0)
+    buf = (abi.tsm_kernel_profile * n)()
+    lib.tsm_profile_read(buf, n)
+    kern = [{"name": b.name.decode(), "launches": b.launches, "seconds": b.seconds, "bytes": b.bytes,
+             "flops": b.flops} for b in buf]
+    kern.sort(key=lambda d: -d["seconds"])
+    total_s = sum(d["seconds"] for d in kern)
+    dom = kern[0]
+    achieved = dom["bytes"] / dom["seconds"] / 1e9
+    roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "us_per_launch": dom["seconds"] / dom["launches"] * 1e6,
+                "bytes_per_launch": dom["bytes"] / dom["launches"],
+                "share_of_step": dom["seconds"] / total_s}
+    kernels = [{"name": d["name"], "launches": d["launches"], "share": round(d["seconds"] / total_s, 4),
+                "GB/s": round(d["bytes"] / d["seconds"] / 1e9, 1),
+                "TFLOP/s": round(d["flops"] / d["seconds"] / 1e12, 2)} for d in kern]
+    dslash = [_dslash_roofline(g, abi, torch, peak, abi.TSM_F16, 1),
+              _dslash_roofline(g, abi, torch, peak, abi.TSM_F16, 12)]
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(dims, w["kappa"], w["mu"], max(lp_iters, 1.0), n_mom)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["workload"], "dims": dims, "eps": w["eps"], "kappa": w["kappa"], "mu": w["mu"],
+                       "lp_solver": "%s storage (links r12, p, Ap), f32 x/r, rho %g" % (args.lp, w["rho_lp"]),
+                       "hp_solver": "f32 CG + f64 reliable updates, rho %g" % w["rho_hp"],
+                       "sources_per_step": {"lp_bulk": args.nrhs, "hp_correction": args.n_hp},
+                       "nrhs_per_launch": args.nrhs, "insertions": 160, "momenta": n_mom,
+                       "l2": "inputs larger than L2 (CG working set %.1f GB)" % (
+                           args.nrhs * g.volume * (96 * 4 + 48 * 2) / 1e9),
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "kernels": kernels[:8],
+            "dslash": dslash,
+            "iterations": {"lp_mean": round(lp_iters, 1), "hp_mean": round(hp_iters, 1)},
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+"""PyTorch-facing wrappers: device memory and streams come from torch, every
+step of the computation runs in the CUDA library through ``abi``.
+
+Fields cross the boundary as torch tensors: plain spinors are complex128
+tensors of shape (nrhs, T, Lz, Ly, Lx, 4, 3); native fields are uint8
+tensors holding the chunked layout described in include/tsm.h.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import abi
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    def __init__(self, device=0):
+        self.device = device
+        torch.cuda.set_device(device)
+        h = ctypes.c_void_p()
+        abi.check(abi.lib().tsm_ctx_create(device, ctypes.byref(h)), "tsm_ctx_create")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            abi.lib().tsm_ctx_destroy(self.handle)
+            self.handle = None
+
+
+class Gauge:
+    """Gauge field on the device in the requested precisions."""
+
+    def __init__(self, ctx, links, dims, t_bc=-1, precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16, abi.TSM_BF16)):
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        lx, ly, lz, lt = self.dims
+        self.volume = lx * ly * lz * lt
+        self.t_bc = t_bc
+        arr = np.ascontiguousarray(links, dtype=np.complex128)
+        assert arr.size == self.volume * 36, "links must hold V*4*3*3 complex numbers"
+        mask = 0
+        for p in precisions:
+            mask |= abi.prec_bit(p)
+        h = ctypes.c_void_p()
+        dims_c = (ctypes.c_int * 4)(*self.dims)
+        abi.check(abi.lib().tsm_create_gauge(ctx.handle, dims_c, arr.ctypes.data_as(ctypes.c_void_p), t_bc, mask,
+                                             ctypes.byref(h)), "tsm_create_gauge")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            abi.lib().tsm_destroy_gauge(self.handle)
+            self.handle = None
+
+    # ---------------------------------------------------------------- fields
+    def field_shape(self, nrhs):
+        lx, ly, lz, lt = self.dims
+        return (nrhs, lt, lz, ly, lx, 4, 3)
+
+    def native_bytes(self, prec, nrhs):
+        return int(abi.lib().tsm_spinor_bytes(self.handle, prec, nrhs))
+
+    def empty_native(self, prec, nrhs):
+        return torch.empty(self.native_bytes(prec, nrhs), dtype=torch.uint8, device="cuda")
+
+    def pack(self, plain, prec, scale=1.0, stream=None):
+        plain = plain.to(device="cuda", dtype=torch.complex128).contiguous()
+        nrhs = plain.shape[0]
+        out = self.empty_native(prec, nrhs)
+        abi.check(abi.lib().tsm_spinor_pack(self.handle, prec, _ptr(plain), _ptr(out), nrhs, scale, _stream(stream)),
+                  "tsm_spinor_pack")
+        return out
+
+    def unpack(self, native, prec, nrhs, scale=1.0, stream=None):
+        out = torch.empty(self.field_shape(nrhs), dtype=torch.complex128, device="cuda")
+        abi.check(abi.lib().tsm_spinor_unpack(self.handle, prec, _ptr(native), _ptr(out), nrhs, scale,
+                                              _stream(stream)), "tsm_spinor_unpack")
+        return out
+
+    # ---------------------------------------------------------------- operators
+    def dslash(self, op, kappa, mu, prec, native_in, nrhs, out=None, stream=None):
+        if out is None:
+            out = self.empty_native(prec, nrhs)
+        abi.check(abi.lib().tsm_dslash_tm(self.handle, kappa, mu, op, prec, _ptr(native_in), _ptr(out), nrhs,
+                                          _stream(stream)), "tsm_dslash_tm")
+        return out
+
+    def sources(self, noise_seed, first_src, nsrc, prec, stream=None):
+        out = self.empty_native(prec, nsrc)
+        abi.check(abi.lib().tsm_make_sources(self.handle, noise_seed, first_src, nsrc, prec, _ptr(out),
+                                             _stream(stream)), "tsm_make_sources")
+        return out
+
+    def solve_sources(self, kappa, mu, solver, rho, noise_seed, first_src, nsrc, max_iter=100000, nrhs_per_launch=0,
+                      out=None, stream=None, allow_not_converged=False):
+        prec = abi.TSM_F64 if solver == abi.TSM_SOLVER_F64 else abi.TSM_F32
+        if out is None:
+            out = self.empty_native(prec, nsrc)
+        stats = (abi.tsm_solve_stats * nsrc)()
+        rc = abi.lib().tsm_solve_sources(self.handle, kappa, mu, solver, rho, max_iter, noise_seed, first_src, nsrc,
+                                         nrhs_per_launch, _ptr(out), stats, _stream(stream))
+        allow = (abi.TSM_ERR_NOT_CONVERGED,) if allow_not_converged else ()
+        abi.check(rc, "tsm_solve_sources", allow)
+        return out, [dict((f, getattr(s, f)) for f, _ in s._fields_) for s in stats]
+
+    def invert(self, op, kappa, mu, solver, rho, native_b, nrhs, max_iter=100000, out=None, stream=None):
+        prec = abi.TSM_F64 if solver == abi.TSM_SOLVER_F64 else abi.TSM_F32
+        if out is None:
+            out = self.empty_native(prec, nrhs)
+        stats = (abi.tsm_solve_stats * nrhs)()
+        abi.check(abi.lib().tsm_invert(self.handle, kappa, mu, op, solver, rho, max_iter, _ptr(native_b), _ptr(out),
+                                       nrhs, stats, _stream(stream)), "tsm_invert")
+        return out, [dict((f, getattr(s, f)) for f, _ in s._fields_) for s in stats]
+
+    def contract(self, kappa, mu, prec, native_s, nsrc, moms, out=None, accumulate=False, stream=None):
+        moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        n_mom = moms.shape[0]
+        if out is None:
+            out = torch.zeros((abi.TSM_N_INSERTIONS, n_mom, self.dims[3], 2), dtype=torch.float64, device="cuda")
+        mom_c = moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        abi.check(abi.lib().tsm_contract_loops(self.handle, kappa, mu, prec, _ptr(native_s), nsrc, n_mom, mom_c,
+                                               _ptr(out), int(accumulate), _stream(stream)), "tsm_contract_loops")
+        return out
+
+    def tsm(self, kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp_solver, hp_solver, noise_seed, moms, max_iter=100000,
+            nrhs_per_launch=12, want_parts=False, stream=None):
+        moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        n_mom = moms.shape[0]
+        p = abi.tsm_params(kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp_solver, hp_solver, noise_seed, max_iter,
+                           nrhs_per_launch, n_mom, moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        loops = np.zeros((abi.TSM_N_INSERTIONS, n_mom, self.dims[3], 2))
+        parts = np.zeros((3, abi.TSM_N_INSERTIONS, n_mom, self.dims[3], 2)) if want_parts else None
+        st = abi.tsm_stats()
+        rc = abi.lib().tsm_solve_tsm(self.handle, ctypes.byref(p), loops.ctypes.data_as(ctypes.c_void_p),
+                                     parts.ctypes.data_as(ctypes.c_void_p) if want_parts else None,
+                                     ctypes.byref(st), _stream(stream))
+        abi.check(rc, "tsm_solve_tsm")
+        stats = dict((f, getattr(st, f)) for f, _ in st._fields_)
+        out = loops[..., 0] + 1j * loops[..., 1]
+        if want_parts:
+            return out, parts[..., 0] + 1j * parts[..., 1], stats
+        return out, stats
+
+
+def momentum_table(p2max=9):
+    n = abi.lib().tsm_momentum_table(p2max, None, 0)
+    buf = (ctypes.c_int * (3 * n))()
+    abi.lib().tsm_momentum_table(p2max, buf, n)
+    return [tuple(buf[3 * k:3 * k + 3]) for k in range(n)]
+
+
+def loops_complex(out):
+    """[160][n_mom][T][2] float64 tensor -> complex128 numpy array."""
+    a = out.detach().cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]

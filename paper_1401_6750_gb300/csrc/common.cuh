@@ -1,0 +1,303 @@
+// Device-side building blocks shared by the kernels of the library:
+// complex arithmetic, the chunked spinor layout, compressed link storage and
+// lattice geometry.  Conventions are those of include/tsm.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "tsm.h"
+
+namespace tsm {
+
+// ---------------------------------------------------------------- complex
+template <typename R>
+struct cplx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cplx<R> mk(R re, R im) {
+  cplx<R> c;
+  c.re = re;
+  c.im = im;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ cplx<R> operator+(cplx<R> a, cplx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename R>
+__device__ __forceinline__ cplx<R> operator-(cplx<R> a, cplx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename R>
+__device__ __forceinline__ cplx<R> operator*(R s, cplx<R> a) { return mk(s * a.re, s * a.im); }
+template <typename R>
+__device__ __forceinline__ cplx<R> cmul(cplx<R> a, cplx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cplx<R> cmulc(cplx<R> a, cplx<R> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cmac(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename R>
+__device__ __forceinline__ void cmacc(cplx<R>& acc, cplx<R> a, cplx<R> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename R>
+__device__ __forceinline__ cplx<R> times_i(cplx<R> a) { return mk(-a.im, a.re); }
+template <typename R>
+__device__ __forceinline__ cplx<R> conjc(cplx<R> a) { return mk(a.re, -a.im); }
+template <typename R>
+__device__ __forceinline__ R norm2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int L[4];  // Lx, Ly, Lz, T
+  int V;
+  int bc;    // temporal boundary sign on the last timeslice
+};
+
+__device__ __forceinline__ void site_coords(const Geom& g, int i, int c[4]) {
+  c[0] = i % g.L[0];
+  int r = i / g.L[0];
+  c[1] = r % g.L[1];
+  r /= g.L[1];
+  c[2] = r % g.L[2];
+  c[3] = r / g.L[2];
+}
+
+// strides of the lexicographic site index
+__device__ __forceinline__ int dir_stride(const Geom& g, int mu) {
+  int s = 1;
+  for (int m = 0; m < mu; ++m) s *= g.L[m];
+  return s;
+}
+
+__device__ __forceinline__ int fwd_site(const Geom& g, int i, const int c[4], int mu, int stride) {
+  return (c[mu] == g.L[mu] - 1) ? i - (g.L[mu] - 1) * stride : i + stride;
+}
+__device__ __forceinline__ int bwd_site(const Geom& g, int i, const int c[4], int mu, int stride) {
+  return (c[mu] == 0) ? i + (g.L[mu] - 1) * stride : i - stride;
+}
+
+// ---------------------------------------------------------------- spinor IO
+// Chunked layout: chunk j of site i of field r at ((r*NCH + j)*V + i)*16 bytes.
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<TSM_F64> {
+  static constexpr int NCH = 12;
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int r, int i, cplx<R> (&v)[12]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 d = __ldg(p + k * V);
+      v[k] = mk<R>((R)d.x, (R)d.y);
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static void store(void* base, size_t V, int r, int i, const cplx<R> (&v)[12]) {
+    double2* p = reinterpret_cast<double2*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k * V] = make_double2((double)v[k].re, (double)v[k].im);
+  }
+};
+
+template <>
+struct SpinorIO<TSM_F32> {
+  static constexpr int NCH = 6;
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int r, int i, cplx<R> (&v)[12]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 d = __ldg(p + k * V);
+      v[2 * k] = mk<R>((R)d.x, (R)d.y);
+      v[2 * k + 1] = mk<R>((R)d.z, (R)d.w);
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static void store(void* base, size_t V, int r, int i, const cplx<R> (&v)[12]) {
+    float4* p = reinterpret_cast<float4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      p[k * V] = make_float4((float)v[2 * k].re, (float)v[2 * k].im, (float)v[2 * k + 1].re,
+                             (float)v[2 * k + 1].im);
+  }
+};
+
+__device__ __forceinline__ float2 h2f(uint32_t w) { return __half22float2(*reinterpret_cast<__half2*>(&w)); }
+__device__ __forceinline__ float2 b2f(uint32_t w) {
+  return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162*>(&w));
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+__device__ __forceinline__ uint32_t f2b(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+template <bool BF>
+struct Half16IO {
+  static constexpr int NCH = 3;
+  __device__ __forceinline__ static float2 cvt(uint32_t w) { return BF ? b2f(w) : h2f(w); }
+  __device__ __forceinline__ static uint32_t pack(float a, float b) { return BF ? f2b(a, b) : f2h(a, b); }
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int r, int i, cplx<R> (&v)[12]) {
+    const uint4* p = reinterpret_cast<const uint4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 d = __ldg(p + k * V);
+      float2 a = cvt(d.x), b = cvt(d.y), c = cvt(d.z), e = cvt(d.w);
+      v[4 * k] = mk<R>(a.x, a.y);
+      v[4 * k + 1] = mk<R>(b.x, b.y);
+      v[4 * k + 2] = mk<R>(c.x, c.y);
+      v[4 * k + 3] = mk<R>(e.x, e.y);
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static void store(void* base, size_t V, int r, int i, const cplx<R> (&v)[12]) {
+    uint4* p = reinterpret_cast<uint4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 d;
+      d.x = pack((float)v[4 * k].re, (float)v[4 * k].im);
+      d.y = pack((float)v[4 * k + 1].re, (float)v[4 * k + 1].im);
+      d.z = pack((float)v[4 * k + 2].re, (float)v[4 * k + 2].im);
+      d.w = pack((float)v[4 * k + 3].re, (float)v[4 * k + 3].im);
+      p[k * V] = d;
+    }
+  }
+};
+template <>
+struct SpinorIO<TSM_F16> : Half16IO<false> {};
+template <>
+struct SpinorIO<TSM_BF16> : Half16IO<true> {};
+
+__host__ __device__ constexpr int spinor_chunks(int p) { return p == TSM_F64 ? 12 : (p == TSM_F32 ? 6 : 3); }
+
+// ---------------------------------------------------------------- links
+// F64: [4][9][V] double2, all entries U_ab (k = 3a + b).
+// F32: [4][3][V] float4, rows 0 and 1 (6 complex, row-major).
+// F16/BF16: [4][V] uint4 (U00, U01, U02, U10) then [4][V] uint2 (U11, U12).
+// Compressed forms rebuild row 2 = conj(row0 x row1).
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(cplx<R> (&u)[3][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+    cplx<R> t = cmul(u[0][c1], u[1][c2]) - cmul(u[0][c2], u[1][c1]);
+    u[2][c] = conjc(t);
+  }
+}
+
+template <int P>
+struct LinkIO;
+
+template <>
+struct LinkIO<TSM_F64> {
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int mu, int i, cplx<R> (&u)[3][3]) {
+    const double2* p = reinterpret_cast<const double2*>(base) + (size_t)mu * 9 * V + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 d = __ldg(p + k * V);
+      u[k / 3][k % 3] = mk<R>((R)d.x, (R)d.y);
+    }
+  }
+};
+
+template <>
+struct LinkIO<TSM_F32> {
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int mu, int i, cplx<R> (&u)[3][3]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)mu * 3 * V + i;
+    float4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * V);
+    u[0][0] = mk<R>(a.x, a.y);
+    u[0][1] = mk<R>(a.z, a.w);
+    u[0][2] = mk<R>(b.x, b.y);
+    u[1][0] = mk<R>(b.z, b.w);
+    u[1][1] = mk<R>(c.x, c.y);
+    u[1][2] = mk<R>(c.z, c.w);
+    reconstruct_row2(u);
+  }
+};
+
+template <bool BF>
+struct Link16IO {
+  __device__ __forceinline__ static float2 cvt(uint32_t w) { return BF ? b2f(w) : h2f(w); }
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int mu, int i, cplx<R> (&u)[3][3]) {
+    const uint4* pa = reinterpret_cast<const uint4*>(base) + (size_t)mu * V + i;
+    const uint2* pb = reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(base) + 4 * V) +
+                      (size_t)mu * V + i;
+    uint4 a = __ldg(pa);
+    uint2 b = __ldg(pb);
+    float2 t;
+    t = cvt(a.x); u[0][0] = mk<R>(t.x, t.y);
+    t = cvt(a.y); u[0][1] = mk<R>(t.x, t.y);
+    t = cvt(a.z); u[0][2] = mk<R>(t.x, t.y);
+    t = cvt(a.w); u[1][0] = mk<R>(t.x, t.y);
+    t = cvt(b.x); u[1][1] = mk<R>(t.x, t.y);
+    t = cvt(b.y); u[1][2] = mk<R>(t.x, t.y);
+    reconstruct_row2(u);
+  }
+};
+template <>
+struct LinkIO<TSM_F16> : Link16IO<false> {};
+template <>
+struct LinkIO<TSM_BF16> : Link16IO<true> {};
+
+// bytes of one device gauge copy of precision p
+inline size_t link_bytes(int p, size_t V) {
+  switch (p) {
+    case TSM_F64: return 4 * 9 * V * 16;
+    case TSM_F32: return 4 * 3 * V * 16;
+    default: return 4 * V * 16 + 4 * V * 8;
+  }
+}
+
+// ---------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum into double (fixed tree). `sh` needs blockDim/32 doubles.
+template <typename T>
+__device__ __forceinline__ double block_sum(T v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = (lane < nw) ? sh[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;  // valid in thread 0
+}
+
+}  // namespace tsm

@@ -1,0 +1,230 @@
+// Field set-up kernels: gauge-copy packing, Z4 noise sources (Philox4x64-10)
+// and conversions between the plain and the chunked spinor layouts.
+#include <math.h>
+
+#include "internal.h"
+
+namespace tsm {
+
+namespace {
+
+constexpr int BS = 256;
+
+// ------------------------------------------------------------------ links
+__global__ void pack_links_f64(const double2* __restrict__ src, double2* __restrict__ dst, int V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int k = 0; k < 9; ++k) dst[((size_t)mu * 9 + k) * V + i] = src[((size_t)i * 4 + mu) * 9 + k];
+}
+
+__global__ void pack_links_f32(const double2* __restrict__ src, float4* __restrict__ dst, int V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  for (int mu = 0; mu < 4; ++mu) {
+    const double2* u = src + ((size_t)i * 4 + mu) * 9;  // row-major 3x3
+    // rows 0 and 1: U00 U01 U02 U10 U11 U12
+    dst[((size_t)mu * 3 + 0) * V + i] = make_float4((float)u[0].x, (float)u[0].y, (float)u[1].x, (float)u[1].y);
+    dst[((size_t)mu * 3 + 1) * V + i] = make_float4((float)u[2].x, (float)u[2].y, (float)u[3].x, (float)u[3].y);
+    dst[((size_t)mu * 3 + 2) * V + i] = make_float4((float)u[4].x, (float)u[4].y, (float)u[5].x, (float)u[5].y);
+  }
+}
+
+template <bool BF>
+__global__ void pack_links_16(const double2* __restrict__ src, uint4* __restrict__ dst, int V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  uint2* dst2 = reinterpret_cast<uint2*>(dst + 4 * (size_t)V);
+  for (int mu = 0; mu < 4; ++mu) {
+    const double2* u = src + ((size_t)i * 4 + mu) * 9;
+    uint32_t w[6];
+    for (int k = 0; k < 6; ++k)
+      w[k] = BF ? f2b((float)u[k].x, (float)u[k].y) : f2h((float)u[k].x, (float)u[k].y);
+    dst[(size_t)mu * V + i] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst2[(size_t)mu * V + i] = make_uint2(w[4], w[5]);
+  }
+}
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Salmon, Moraes, Dror, Shaw, SC'11: round (X0..X3) -> (hi(M1 X2) ^ X1 ^ K0,
+// lo(M1 X2), hi(M0 X0) ^ X3 ^ K1, lo(M0 X0)); key += Weyl constants between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t (&x)[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t lo0 = M0 * x[0], hi0 = __umul64hi(M0, x[0]);
+    const uint64_t lo1 = M1 * x[2], hi1 = __umul64hi(M1, x[2]);
+    const uint64_t n0 = hi1 ^ x[1] ^ k0, n2 = hi0 ^ x[3] ^ k1;
+    x[0] = n0;
+    x[1] = lo1;
+    x[2] = n2;
+    x[3] = lo0;
+  }
+}
+
+template <int P>
+__global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= V) return;
+  uint64_t x[4] = {(uint64_t)i, 0ull, 0ull, 0ull};
+  philox4x64_10(x, seed, first + (uint64_t)r);
+  const uint64_t w = x[0];
+  cplx<double> v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int z = (int)((w >> (2 * k)) & 3ull);
+    // i^z: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
+    v[k] = mk<double>(z == 0 ? 1.0 : (z == 2 ? -1.0 : 0.0), z == 1 ? 1.0 : (z == 3 ? -1.0 : 0.0));
+  }
+  SpinorIO<P>::store(out, (size_t)V, r, i, v);
+}
+
+// ------------------------------------------------------------------ layout conversions
+template <int P>
+__global__ void pack_kernel(const double2* __restrict__ plain, void* native, int V, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= V) return;
+  cplx<double> v[12];
+  const double2* p = plain + ((size_t)r * V + i) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) v[k] = mk<double>(p[k].x * scale, p[k].y * scale);
+  SpinorIO<P>::store(native, (size_t)V, r, i, v);
+}
+
+template <int P>
+__global__ void unpack_kernel(const void* native, double2* __restrict__ plain, int V, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= V) return;
+  cplx<double> v[12];
+  SpinorIO<P>::load(native, (size_t)V, r, i, v);
+  double2* p = plain + ((size_t)r * V + i) * 12;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = make_double2(v[k].re * scale, v[k].im * scale);
+}
+
+template <int PD, int PS>
+__global__ void convert_kernel(void* dst, const void* src, int V, int gamma5) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= V) return;
+  cplx<double> v[12];
+  SpinorIO<PS>::load(src, (size_t)V, r, i, v);
+  if (gamma5) {
+#pragma unroll
+    for (int k = 6; k < 12; ++k) v[k] = mk<double>(-v[k].re, -v[k].im);
+  }
+  SpinorIO<PD>::store(dst, (size_t)V, r, i, v);
+}
+
+template <int PD>
+int convert_from(int ps, void* dst, const void* src, int V, int nrhs, int gamma5, cudaStream_t s) {
+  dim3 grid((V + BS - 1) / BS, nrhs);
+  count_launches(1);
+  switch (ps) {
+    case TSM_F64: convert_kernel<PD, TSM_F64><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
+    case TSM_F32: convert_kernel<PD, TSM_F32><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
+    case TSM_F16: convert_kernel<PD, TSM_F16><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
+    case TSM_BF16: convert_kernel<PD, TSM_BF16><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", ps);
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+}  // namespace
+
+int build_links(tsm_gauge* g, const double* links_host) {
+  const int V = g->geom.V;
+  const size_t host_bytes = (size_t)V * 4 * 9 * sizeof(double2);
+  DevBuf staging;
+  TSM_TRY(staging.reserve(host_bytes));
+  TSM_CUDA(cudaMemcpy(staging.p, links_host, host_bytes, cudaMemcpyHostToDevice));
+  const int nb = (V + BS - 1) / BS;
+  for (int p = 0; p < 4; ++p) {
+    if (!has_prec(g, p)) continue;
+    TSM_TRY(g->links[p].reserve(link_bytes(p, V)));
+    count_launches(1);
+    const double2* src = staging.as<double2>();
+    switch (p) {
+      case TSM_F64: pack_links_f64<<<nb, BS>>>(src, g->links[p].as<double2>(), V); break;
+      case TSM_F32: pack_links_f32<<<nb, BS>>>(src, g->links[p].as<float4>(), V); break;
+      case TSM_F16: pack_links_16<false><<<nb, BS>>>(src, g->links[p].as<uint4>(), V); break;
+      case TSM_BF16: pack_links_16<true><<<nb, BS>>>(src, g->links[p].as<uint4>(), V); break;
+    }
+    TSM_CUDA(cudaGetLastError());
+  }
+  TSM_CUDA(cudaDeviceSynchronize());
+  return TSM_OK;
+}
+
+int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* out,
+                 cudaStream_t s) {
+  const int V = g->geom.V;
+  dim3 grid((V + BS - 1) / BS, nsrc);
+  count_launches(1);
+  switch (prec) {
+    case TSM_F64: z4_kernel<TSM_F64><<<grid, BS, 0, s>>>(seed, first, V, out); break;
+    case TSM_F32: z4_kernel<TSM_F32><<<grid, BS, 0, s>>>(seed, first, V, out); break;
+    case TSM_F16: z4_kernel<TSM_F16><<<grid, BS, 0, s>>>(seed, first, V, out); break;
+    case TSM_BF16: z4_kernel<TSM_BF16><<<grid, BS, 0, s>>>(seed, first, V, out); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+int spinor_pack(const tsm_gauge* g, int prec, const double* plain, void* native, int nrhs, double scale,
+                cudaStream_t s) {
+  const int V = g->geom.V;
+  dim3 grid((V + BS - 1) / BS, nrhs);
+  count_launches(1);
+  const double2* src = reinterpret_cast<const double2*>(plain);
+  switch (prec) {
+    case TSM_F64: pack_kernel<TSM_F64><<<grid, BS, 0, s>>>(src, native, V, scale); break;
+    case TSM_F32: pack_kernel<TSM_F32><<<grid, BS, 0, s>>>(src, native, V, scale); break;
+    case TSM_F16: pack_kernel<TSM_F16><<<grid, BS, 0, s>>>(src, native, V, scale); break;
+    case TSM_BF16: pack_kernel<TSM_BF16><<<grid, BS, 0, s>>>(src, native, V, scale); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+int spinor_unpack(const tsm_gauge* g, int prec, const void* native, double* plain, int nrhs, double scale,
+                  cudaStream_t s) {
+  const int V = g->geom.V;
+  dim3 grid((V + BS - 1) / BS, nrhs);
+  count_launches(1);
+  double2* dst = reinterpret_cast<double2*>(plain);
+  switch (prec) {
+    case TSM_F64: unpack_kernel<TSM_F64><<<grid, BS, 0, s>>>(native, dst, V, scale); break;
+    case TSM_F32: unpack_kernel<TSM_F32><<<grid, BS, 0, s>>>(native, dst, V, scale); break;
+    case TSM_F16: unpack_kernel<TSM_F16><<<grid, BS, 0, s>>>(native, dst, V, scale); break;
+    case TSM_BF16: unpack_kernel<TSM_BF16><<<grid, BS, 0, s>>>(native, dst, V, scale); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+int spinor_convert(const tsm_gauge* g, int pd, void* dst, int ps, const void* src, int nrhs, int gamma5,
+                   cudaStream_t s) {
+  const int V = g->geom.V;
+  switch (pd) {
+    case TSM_F64: return convert_from<TSM_F64>(ps, dst, src, V, nrhs, gamma5, s);
+    case TSM_F32: return convert_from<TSM_F32>(ps, dst, src, V, nrhs, gamma5, s);
+    case TSM_F16: return convert_from<TSM_F16>(ps, dst, src, V, nrhs, gamma5, s);
+    case TSM_BF16: return convert_from<TSM_BF16>(ps, dst, src, V, nrhs, gamma5, s);
+  }
+  return fail(TSM_ERR_INVALID_ARG, "bad precision %d", pd);
+}
+
+}  // namespace tsm

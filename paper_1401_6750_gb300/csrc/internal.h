@@ -1,0 +1,161 @@
+// Host-side internals shared by the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+#include "tsm.h"
+
+namespace tsm {
+
+// Record a message for tsm_last_error() and return `code`.
+int fail(int code, const char* fmt, ...);
+int cuda_status(cudaError_t e, const char* what, const char* file, int line);
+
+#define TSM_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::tsm::cuda_status(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define TSM_TRY(expr)            \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != TSM_OK) return rc_; \
+  } while (0)
+
+// Owning device allocation.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // Grow to at least n bytes (contents are not kept).
+  int reserve(size_t n);
+  template <typename T>
+  T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+// Per right-hand-side solver state, resident on the device.
+struct RhsState {
+  double rr;       // |r|^2 of the iterated residual
+  double bb;       // |b|^2
+  double rho2bb;   // stop threshold rho^2 |b|^2
+  double alpha, beta;
+  double sigma;    // stored sloppy p and Ap are p / sigma, Ap / sigma
+  double c_r, c_p; // p_new / sigma_new = c_r r + c_p (p_old / sigma_old)
+  double r_max2;   // largest |r|^2 since the last residual replacement
+  double true_rr;  // |r_true|^2 at the last replacement
+  double delta2;   // replacement trigger: |r|^2 < delta^2 r_max2
+  int iter, max_iter;
+  int active;      // 1 while iterating
+  int need_ru;     // residual replacement requested
+  int status;      // see SolveStatus
+  int n_ru, restarts, restart_p;
+};
+
+enum SolveStatus { ST_RUNNING = 0, ST_ITER_CONV = 1, ST_MAXITER = 2, ST_DONE = 3, ST_FAILED = 4, ST_BREAKDOWN = 5 };
+
+struct SolverWorkspace;    // solver.cu
+struct ContractWorkspace;  // contract.cu
+struct SolverWsDeleter {
+  void operator()(SolverWorkspace* w) const;  // solver.cu
+};
+struct ContractWsDeleter {
+  void operator()(ContractWorkspace* w) const;  // contract.cu
+};
+
+}  // namespace tsm
+
+struct tsm_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;  // blocking stream used when the caller passes NULL
+  int sm_count = 0;
+};
+
+struct tsm_gauge {
+  tsm_ctx* ctx = nullptr;
+  tsm::Geom geom{};
+  unsigned precisions = 0;
+  tsm::DevBuf links[4];
+  std::mutex mu;  // guards the caches below
+  std::map<long long, std::unique_ptr<tsm::SolverWorkspace, tsm::SolverWsDeleter>> solver_ws;
+  std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws;
+  tsm::DevBuf tmp;  // operator scratch (M^dag M intermediate, conversions)
+  std::mutex tsm_mu;       // guards the TSM buffers
+  tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
+  tsm::DevBuf tsm_sol;     // solutions of one batch
+  ~tsm_gauge();
+};
+
+namespace tsm {
+
+inline cudaStream_t pick_stream(const tsm_gauge* g, void* s) {
+  return s ? reinterpret_cast<cudaStream_t>(s) : g->ctx->stream;
+}
+inline bool has_prec(const tsm_gauge* g, int p) { return (g->precisions >> p) & 1u; }
+
+// ---- launchers (dslash.cu)
+int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
+                 cudaStream_t s);
+// out = op in with the link copy `prec_links` (may differ from the field precision `prec_field` only in
+// the combinations instantiated there); gamma5 != 0 stores g5 * result.
+int dslash_apply_mixed(tsm_gauge* g, int prec_field, int prec_links, int op, double kappa, double mu,
+                       const void* in, void* out, int nrhs, int gamma5, cudaStream_t s);
+
+// ---- fields (fields.cu)
+int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* out, cudaStream_t s);
+int spinor_pack(const tsm_gauge* g, int prec, const double* plain, void* native, int nrhs, double scale,
+                cudaStream_t s);
+int spinor_unpack(const tsm_gauge* g, int prec, const void* native, double* plain, int nrhs, double scale,
+                  cudaStream_t s);
+// dst(prec_dst) = a * src(prec_src) (+ g5 if gamma5), nrhs fields
+int spinor_convert(const tsm_gauge* g, int prec_dst, void* dst, int prec_src, const void* src, int nrhs,
+                   int gamma5, cudaStream_t s);
+int build_links(tsm_gauge* g, const double* links_host);
+
+// ---- solver (solver.cu)
+// Solve M(mu) x = eta for nrhs right-hand sides.  eta (device, native layout of
+// eta_prec) or, when eta is null, the Z4 sources (seed, first .. first+nrhs-1).
+// gamma5_io != 0 multiplies eta by g5 on input and x by g5 on output.
+int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
+                     const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
+                     int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
+int solver_precise_prec(int solver);
+int solver_output_prec(int solver);
+unsigned solver_link_precs(int solver);
+
+// ---- contraction (contract.cu)
+int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
+                   const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
+
+// ---- misc
+int momentum_table(int p2max, std::vector<int>& out);
+
+// ---- profiling (prof.cu)
+bool profiling();
+void count_launches(long long n);  // kernels enqueued by the library (graph nodes included)
+void prof_add(const char* name, double seconds, double bytes, double flops);
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  int begin(cudaStream_t s);
+  int end(cudaStream_t s);
+  double seconds();  // waits for the end event
+  ~EventPair();
+};
+inline double spinor_site_bytes(int prec) { return 16.0 * spinor_chunks(prec); }
+inline double link_site_bytes(int prec) { return (double)link_bytes(prec, 1); }
+
+}  // namespace tsm

@@ -1,0 +1,149 @@
+// Truncated Solver Method driver (Sec. 2.1) with on-device accumulation of
+// the contractions (the "projected scheme" of Fig. 4: sources, inversions,
+// contractions, accumulation and the Fourier projection all stay on the GPU;
+// only the final estimate crosses to the host).
+//
+//   E = (1/N_LP) sum_{r < N_LP} L_LP(eta_r)
+//     + (1/N_HP) sum_{N_LP <= r < N_LP + N_HP} [ L_HP(eta_r) - L_LP(eta_r) ]
+//
+// The low-precision map is the same solver call (same precision, stopping
+// rule, x0 = 0 and fixed-order reductions) for bulk and correction sources,
+// and each right-hand side's arithmetic does not depend on its batch mates,
+// so the correction term is an unbiased estimate of the LP bias.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "internal.h"
+
+namespace tsm {
+
+namespace {
+
+__global__ void combine_kernel(const double* __restrict__ bulk, const double* __restrict__ hp,
+                               const double* __restrict__ lpc, double inv_lp, double inv_hp, size_t n,
+                               double* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double e = bulk[i] * inv_lp;
+  if (inv_hp != 0.0) e += (hp[i] - lpc[i]) * inv_hp;
+  out[i] = e;
+}
+
+struct Accum {
+  int iters_total = 0, iters_max = 0, not_conv = 0;
+  double res_max = 0.0;
+  void add(const std::vector<tsm_solve_stats>& st, int n) {
+    for (int k = 0; k < n; ++k) {
+      iters_total += st[k].iterations;
+      iters_max = std::max(iters_max, st[k].iterations);
+      res_max = std::max(res_max, st[k].true_residual);
+      not_conv += !st[k].converged;
+    }
+  }
+};
+
+// Solve sources [first, first + n) with `solver` and add their loops to acc.
+int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho, uint64_t first, int n,
+                       int batch, DevBuf& sol, double* acc, Accum& a, cudaStream_t s) {
+  const int op = solver_output_prec(solver);
+  std::vector<tsm_solve_stats> st(batch);
+  for (int k0 = 0; k0 < n; k0 += batch) {
+    const int nb = std::min(batch, n - k0);
+    TSM_TRY(sol.reserve(tsm_spinor_bytes(g, op, nb)));
+    int rc = solve_batch_impl(g, p->kappa, p->mu, solver, rho, p->max_iter, nb, nullptr, 0, p->noise_seed,
+                              first + k0, op, sol.p, 0, st.data(), s);
+    if (rc != TSM_OK && rc != TSM_ERR_NOT_CONVERGED) return rc;
+    a.add(st, nb);
+    TSM_TRY(contract_loops(g, p->kappa, p->mu, op, sol.p, nb, p->n_mom, p->mom, acc, 1, s));
+  }
+  return TSM_OK;
+}
+
+}  // namespace
+
+}  // namespace tsm
+
+using namespace tsm;
+
+namespace tsm {
+
+// Shared body: the estimate is left in est_dev (device) and, when the host
+// pointers are given, copied out.
+static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* parts_dev, double* loops_host,
+                   double* parts_host, tsm_stats* stats, void* stream) {
+  if (!g || !p) return fail(TSM_ERR_INVALID_ARG, "tsm_solve_tsm: NULL argument");
+  if (p->n_lp < 1 || p->n_hp < 0) return fail(TSM_ERR_INVALID_ARG, "need n_lp >= 1 and n_hp >= 0");
+  if (p->n_mom < 1 || !p->mom) return fail(TSM_ERR_INVALID_ARG, "need at least one momentum");
+  for (int solver : {p->lp_solver, p->hp_solver}) {
+    if (solver < TSM_SOLVER_F64 || solver > TSM_SOLVER_LP_BF16) return fail(TSM_ERR_INVALID_ARG, "bad solver");
+    const unsigned need = solver_link_precs(solver);
+    if ((g->precisions & need) != need)
+      return fail(TSM_ERR_INVALID_ARG, "solver %d needs gauge copies 0x%x", solver, need);
+  }
+  if (!(p->rho_lp > 0 && p->rho_lp < 1) || !(p->rho_hp > 0 && p->rho_hp < 1))
+    return fail(TSM_ERR_INVALID_ARG, "rho_lp and rho_hp must lie in (0, 1)");
+  if (p->max_iter < 1 || !(p->kappa > 0) || !isfinite(p->mu)) return fail(TSM_ERR_INVALID_ARG, "bad max_iter/kappa/mu");
+  TSM_CUDA(cudaSetDevice(g->ctx->device));
+  cudaStream_t s = pick_stream(g, stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int batch = p->nrhs_per_launch > 0 ? std::min(p->nrhs_per_launch, 1024) : 12;
+  const size_t n_out = (size_t)160 * p->n_mom * g->geom.L[3] * 2;
+  std::lock_guard<std::mutex> lock(g->tsm_mu);
+  TSM_TRY(g->tsm_acc.reserve(sizeof(double) * n_out * 4));
+  double* bulk = g->tsm_acc.as<double>();
+  double* hp = bulk + n_out;
+  double* lpc = hp + n_out;
+  double* est = est_dev ? est_dev : lpc + n_out;
+  TSM_CUDA(cudaMemsetAsync(bulk, 0, sizeof(double) * n_out * 3, s));
+  Accum lp_a, hp_a;
+  DevBuf& sol = g->tsm_sol;
+  TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, 0, p->n_lp, batch, sol, bulk, lp_a, s));
+  if (p->n_hp > 0) {
+    TSM_TRY(solve_and_contract(g, p, p->hp_solver, p->rho_hp, (uint64_t)p->n_lp, p->n_hp, batch, sol, hp, hp_a, s));
+    TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, (uint64_t)p->n_lp, p->n_hp, batch, sol, lpc, lp_a, s));
+  }
+  const int bs = 256;
+  count_launches(1);
+  combine_kernel<<<(unsigned)((n_out + bs - 1) / bs), bs, 0, s>>>(bulk, hp, lpc, 1.0 / p->n_lp,
+                                                                  p->n_hp ? 1.0 / p->n_hp : 0.0, n_out, est);
+  TSM_CUDA(cudaGetLastError());
+  if (parts_dev) TSM_CUDA(cudaMemcpyAsync(parts_dev, bulk, sizeof(double) * n_out * 3, cudaMemcpyDeviceToDevice, s));
+  if (loops_host) TSM_CUDA(cudaMemcpyAsync(loops_host, est, sizeof(double) * n_out, cudaMemcpyDeviceToHost, s));
+  if (parts_host) TSM_CUDA(cudaMemcpyAsync(parts_host, bulk, sizeof(double) * n_out * 3, cudaMemcpyDeviceToHost, s));
+  if (loops_host || parts_host || stats) TSM_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->lp_iterations_total = lp_a.iters_total;
+    stats->lp_max_iterations = lp_a.iters_max;
+    stats->lp_max_true_residual = lp_a.res_max;
+    stats->hp_iterations_total = hp_a.iters_total;
+    stats->hp_max_iterations = hp_a.iters_max;
+    stats->hp_max_true_residual = hp_a.res_max;
+    stats->n_not_converged = lp_a.not_conv + hp_a.not_conv;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (loops_host)
+    for (size_t k = 0; k < n_out; ++k)
+      if (!isfinite(loops_host[k])) return fail(TSM_ERR_NONFINITE, "non-finite loop value");
+  if (lp_a.not_conv + hp_a.not_conv)
+    return fail(TSM_ERR_NOT_CONVERGED, "%d solves missed rho", lp_a.not_conv + hp_a.not_conv);
+  return TSM_OK;
+}
+
+}  // namespace tsm
+
+extern "C" int tsm_solve_tsm(tsm_gauge* g, const tsm_params* p, double* loops_host, double* parts_host,
+                             tsm_stats* stats, void* stream) {
+  if (!loops_host) return fail(TSM_ERR_INVALID_ARG, "tsm_solve_tsm: loops_host is NULL");
+  return run_tsm(g, p, nullptr, nullptr, loops_host, parts_host, stats, stream);
+}
+
+extern "C" int tsm_solve_tsm_dev(tsm_gauge* g, const tsm_params* p, double* loops_dev, double* parts_dev,
+                                 tsm_stats* stats, void* stream) {
+  if (!loops_dev) return fail(TSM_ERR_INVALID_ARG, "tsm_solve_tsm_dev: loops_dev is NULL");
+  return run_tsm(g, p, loops_dev, parts_dev, nullptr, nullptr, stats, stream);
+}

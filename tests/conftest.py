@@ -9,3 +9,26 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: oracle cases that take more than a few seconds")
+
+
+import numpy as np
+import pytest
+
+
+def rel_err(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """CUDA context of the library on device 0 (GPU tests only)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1401_6750_gb300 import api, build
+    build.build()
+    c = api.Context(0)
+    yield c
+    c.close()
