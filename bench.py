@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,T (default 24,24,24,48)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--probe", default=None, choices=["dslash", "tsm"],
+                    help="run a few launches of one kernel family for an ncu capture and exit")
     return ap.parse_args()
 
 
@@ -214,10 +216,39 @@ def _dslash_roofline(g, abi, torch, peak, prec, nrhs, reps=10):
             "bytes_per_launch": bytes_, "us_per_launch": t * 1e6, "l2": "flushed (512 MB write) before each launch"}
 
 
+def probe(args):
+    """Small, self-contained workloads for profiler captures (no timing output)."""
+    import ctypes
+
+    import torch
+    from paper_1401_6750_gb300 import abi, api, build, synth
+    build.build()
+    dims = [int(v) for v in args.dims.split(",")] if args.dims else WORKLOAD["dims"]
+    links = synth.gauge_links(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
+    ctx = api.Context(0)
+    g = api.Gauge(ctx, links, dims, WORKLOAD["t_bc"], precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16,
+                                                                   abi.TSM_BF16))
+    if args.probe == "dslash":
+        prec = abi.TSM_F16 if args.lp == "f16" else abi.TSM_BF16
+        src = g.sources(5, 0, args.nrhs, prec)
+        for _ in range(3):
+            g.dslash(abi.TSM_OP_M, WORKLOAD["kappa"], WORKLOAD["mu"], prec, src, args.nrhs)
+    else:
+        lp = abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16
+        g.tsm(WORKLOAD["kappa"], WORKLOAD["mu"], args.nrhs, args.n_hp, WORKLOAD["rho_lp"], WORKLOAD["rho_hp"], lp,
+              abi.TSM_SOLVER_F32_RELIABLE, 11, api.momentum_table(9), nrhs_per_launch=args.nrhs)
+    torch.cuda.synchronize()
+    g.close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.probe:
+        probe(args)
         return
     import ctypes
 

@@ -146,8 +146,9 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src,
  * residual (recomputed with the precise operator: FP64 for F64 and
  * F32_RELIABLE, FP32 for the LP solvers) confirms it; otherwise the
  * iteration restarts from the true residual, up to max_iter in total.
- * Solutions are written in native layout: F64 for TSM_SOLVER_F64, F32
- * otherwise.  stats_host (optional) receives nsrc records.  Returns
+ * Solutions are written in native layout: F64 for TSM_SOLVER_F64 and
+ * TSM_SOLVER_F32_RELIABLE (its FP64 accumulated solution), F32 for the LP
+ * solvers.  stats_host (optional) receives nsrc records.  Returns
  * TSM_ERR_NOT_CONVERGED if any source missed rho (outputs still written).
  * Right-hand sides are batched `nrhs_per_launch` at a time (<= 0: all). */
 int tsm_solve_sources(tsm_gauge* g, double kappa, double mu, int solver,
@@ -157,8 +158,9 @@ int tsm_solve_sources(tsm_gauge* g, double kappa, double mu, int solver,
 
 /* Solve op x = b for caller right-hand sides, op = TSM_OP_M (M x = b) or
  * TSM_OP_MDAG (M^dag x = b, through M^dag = g5 M(-mu) g5).  b and x in the
- * native layout of the solver's output precision (F64 for TSM_SOLVER_F64,
- * F32 otherwise).  Same stopping rule as tsm_solve_sources. */
+ * native layout of the solver's output precision (F64 for TSM_SOLVER_F64 and
+ * TSM_SOLVER_F32_RELIABLE, F32 for the LP solvers).  Same stopping rule as
+ * tsm_solve_sources. */
 int tsm_invert(tsm_gauge* g, double kappa, double mu, int op, int solver,
                double rho, int max_iter, const void* b_dev, void* x_dev,
                int nrhs, tsm_solve_stats* stats_host, void* stream);

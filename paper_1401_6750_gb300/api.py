@@ -18,6 +18,11 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def solution_prec(solver):
+    """Native precision of the solutions a solver returns."""
+    return abi.TSM_F64 if solver in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+
+
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
@@ -102,7 +107,7 @@ class Gauge:
 
     def solve_sources(self, kappa, mu, solver, rho, noise_seed, first_src, nsrc, max_iter=100000, nrhs_per_launch=0,
                       out=None, stream=None, allow_not_converged=False):
-        prec = abi.TSM_F64 if solver == abi.TSM_SOLVER_F64 else abi.TSM_F32
+        prec = solution_prec(solver)
         if out is None:
             out = self.empty_native(prec, nsrc)
         stats = (abi.tsm_solve_stats * nsrc)()
@@ -113,7 +118,7 @@ class Gauge:
         return out, [dict((f, getattr(s, f)) for f, _ in s._fields_) for s in stats]
 
     def invert(self, op, kappa, mu, solver, rho, native_b, nrhs, max_iter=100000, out=None, stream=None):
-        prec = abi.TSM_F64 if solver == abi.TSM_SOLVER_F64 else abi.TSM_F32
+        prec = solution_prec(solver)
         if out is None:
             out = self.empty_native(prec, nrhs)
         stats = (abi.tsm_solve_stats * nrhs)()

@@ -150,6 +150,8 @@ int tsm_create_gauge(tsm_ctx* ctx, const int dims[4], const double* links_host, 
   // the links must be finite SU(3) matrices (the 12-real copies rebuild row 3)
   for (long long k = 0; k < v * 4; ++k) {
     const double* u = links_host + k * 18;
+    for (int c = 0; c < 18; ++c)
+      if (!isfinite(u[c])) return fail(TSM_ERR_NONFINITE, "link %lld is not finite", k);
     double dev = 0.0;
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
@@ -162,10 +164,7 @@ int tsm_create_gauge(tsm_ctx* ctx, const int dims[4], const double* links_host, 
         }
         dev = std::max(dev, fabs(re - (a == b ? 1.0 : 0.0)) + fabs(im));
       }
-    if (!(dev < 1e-6)) {
-      if (!isfinite(dev)) return fail(TSM_ERR_NONFINITE, "link %lld is not finite", k);
-      return fail(TSM_ERR_INVALID_ARG, "link %lld is not unitary (|UU^dag - 1| = %g)", k, dev);
-    }
+    if (!(dev < 1e-6)) return fail(TSM_ERR_INVALID_ARG, "link %lld is not unitary (|UU^dag - 1| = %g)", k, dev);
   }
   TSM_CUDA(cudaSetDevice(ctx->device));
   tsm_gauge* g = new tsm_gauge();

@@ -15,6 +15,7 @@ int launch_store(const tsm_gauge* g, double kappa, double tw, const void* in, vo
   a.links = g->links[PL].p;
   a.in = in;
   a.nblk = (g->geom.V + DSLASH_BS - 1) / DSLASH_BS;
+  a.nrhs = nrhs;
   a.kappa = kappa;
   a.tw = tw;
   EpiStore<R, PO> e;

@@ -10,9 +10,10 @@
 // two-spin vector h, the colour matrix acts on h only, and the lower two
 // spins are rebuilt from the upper ones.
 //
-// Thread mapping: one thread per (site, right-hand side); blockIdx.y is the
-// right-hand side, so the blocks of all right-hand sides of one site tile
-// are scheduled back to back and share the links through L2.
+// Thread mapping: one thread per (site, right-hand side).  The block index
+// runs over (site tile, right-hand side) with the right-hand side fastest, so
+// the blocks of all right-hand sides of one site tile are scheduled back to
+// back and re-read that tile's links from L2 rather than from HBM.
 #pragma once
 
 #include "common.cuh"
@@ -26,6 +27,7 @@ struct DslashArgs {
   const void* links;  // device links in the kernel's link precision
   const void* in;     // input field(s), native layout
   int nblk;           // blocks along the site axis
+  int nrhs;           // right-hand sides in the launch
   double kappa;
   double tw;          // twist coefficient multiplying i g5
 };
@@ -150,11 +152,11 @@ __device__ __forceinline__ void apply_site(cplx<R> (&out)[12], const DslashArgs&
 // (deterministic for a fixed grid) and calls epi.finalize(rhs, total).
 template <class Epi>
 __device__ __forceinline__ void reduce_and_finalize(const Epi& epi, const RedSlots& red, int rhs, int nblk,
-                                                    double v, double* sh) {
+                                                    int blk, double v, double* sh) {
   __shared__ bool is_last;
   double bs = block_sum(v, sh);
   if (threadIdx.x == 0) {
-    red.partial[(size_t)rhs * nblk + blockIdx.x] = bs;
+    red.partial[(size_t)rhs * nblk + blk] = bs;
     __threadfence();
     unsigned t = atomicAdd(&red.counter[rhs], 1u);
     is_last = (t == (unsigned)(nblk - 1));
@@ -181,16 +183,17 @@ __device__ __forceinline__ void reduce_and_finalize(const Epi& epi, const RedSlo
 template <typename R, int SF, int PIN, int PL, class Epi>
 __global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi) {
   __shared__ double sh[32];
-  const int rhs = blockIdx.y;
+  const int rhs = blockIdx.x % a.nrhs;
+  const int blk = blockIdx.x / a.nrhs;
   if (!epi.active(rhs)) return;
-  const int i = blockIdx.x * DSLASH_BS + threadIdx.x;
+  const int i = blk * DSLASH_BS + threadIdx.x;
   R red = (R)0;
   if (i < a.g.V) {
     cplx<R> out[12];
     apply_site<SF, R, PIN, PL>(out, a, rhs, i);
     red = epi.site(rhs, i, out);
   }
-  if (Epi::kReduce) reduce_and_finalize(epi, epi.red, rhs, a.nblk, (double)red, sh);
+  if (Epi::kReduce) reduce_and_finalize(epi, epi.red, rhs, a.nblk, blk, (double)red, sh);
 }
 
 // Plain store of the result (optionally times g5), no reduction.
@@ -213,6 +216,6 @@ struct EpiStore {
   __device__ void finalize(int, double) const {}
 };
 
-inline dim3 dslash_grid(int V, int nrhs) { return dim3((V + DSLASH_BS - 1) / DSLASH_BS, nrhs, 1); }
+inline dim3 dslash_grid(int V, int nrhs) { return dim3((unsigned)((V + DSLASH_BS - 1) / DSLASH_BS) * nrhs, 1, 1); }
 
 }  // namespace tsm

@@ -416,7 +416,9 @@ void SolverWsDeleter::operator()(SolverWorkspace* w) const { delete w; }
 int solver_precise_prec(int solver) {
   return (solver == TSM_SOLVER_F64 || solver == TSM_SOLVER_F32_RELIABLE) ? TSM_F64 : TSM_F32;
 }
-int solver_output_prec(int solver) { return solver == TSM_SOLVER_F64 ? TSM_F64 : TSM_F32; }
+int solver_output_prec(int solver) {
+  return (solver == TSM_SOLVER_F64 || solver == TSM_SOLVER_F32_RELIABLE) ? TSM_F64 : TSM_F32;
+}
 unsigned solver_link_precs(int solver) {
   switch (solver) {
     case TSM_SOLVER_F64: return TSM_PREC_BIT(TSM_F64);
@@ -479,11 +481,12 @@ struct Solver {
     return TSM_OK;
   }
 
-  static DslashArgs args(const tsm_gauge* g, int pl, const void* in, double kappa, double tw) {
+  static DslashArgs args(const tsm_gauge* g, int pl, const void* in, double kappa, double tw, int nrhs) {
     DslashArgs a;
     a.g = g->geom;
     a.links = g->links[pl].p;
     a.in = in;
+    a.nrhs = nrhs;
     a.nblk = (g->geom.V + DSLASH_BS - 1) / DSLASH_BS;
     a.kappa = kappa;
     a.tw = tw;
@@ -511,12 +514,12 @@ struct Solver {
     {
       EpiMp<Rs, T::PS> e{w.q.p, V, w.st.as<RhsState>(), slots(w)};
       dslash_kernel<Rs, -1, T::PS, T::PLs, EpiMp<Rs, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup, nrhs), e);
     }
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, V, w.st.as<RhsState>(), slots(w), prm};
       dslash_kernel<Rs, +1, T::PS, T::PLs, EpiCG<Rs, T::PA, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e);
     }
     dim3 eg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 0, g->geom.V);
@@ -537,14 +540,14 @@ struct Solver {
     {
       EpiMp<Rs, T::PS> e{w.q.p, V, w.st.as<RhsState>(), slots(w)};
       dslash_kernel<Rs, -1, T::PS, T::PLs, EpiMp<Rs, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup, nrhs), e);
     }
     TSM_TRY(e1.end(s));
     TSM_TRY(e2.begin(s));
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, V, w.st.as<RhsState>(), slots(w), prm};
       dslash_kernel<Rs, +1, T::PS, T::PLs, EpiCG<Rs, T::PA, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e);
     }
     TSM_TRY(e2.end(s));
     TSM_TRY(e3.begin(s));
@@ -612,12 +615,12 @@ struct Solver {
     {
       EpiStoreMasked<Rp, T::PP> e{w.t.p, V, w.mask.as<int>(), RedSlots{nullptr, nullptr}};
       dslash_kernel<Rp, -1, T::PX, T::PLp, EpiStoreMasked<Rp, T::PP>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, xsrc, kappa, mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, xsrc, kappa, mup, nrhs), e);
     }
     {
       EpiResidual<Rp, T::PP, T::PA> e{w.b.p, w.r.p, V, w.mask.as<int>(), w.st.as<RhsState>(), slots(w), prm};
       dslash_kernel<Rp, +1, T::PP, T::PLp, EpiResidual<Rp, T::PP, T::PA>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e);
     }
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 1, g->geom.V);
     TSM_CUDA(cudaGetLastError());
@@ -637,7 +640,7 @@ struct Solver {
     {
       EpiInitB<Rp, T::PP> e{w.b.p, V, w.st.as<RhsState>(), slots(w), prm};
       dslash_kernel<Rp, +1, T::PP, T::PLp, EpiInitB<Rp, T::PP>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup), e);
+          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e);
     }
     k_init<T::PP, T::PA, T::PS, T::XACC>
         <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.as<double2>(), w.st.as<RhsState>(), g->geom.V);
@@ -672,10 +675,10 @@ struct Solver {
       }
     }
     count_launches(1);
-    k_output<T::PA, T::PA, T::XACC><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.t.p, gamma5_out,
+    // solution (x_acc + x for the reliable-update solver) in the precise precision, into w.t
+    k_output<T::PA, T::PP, T::XACC><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.t.p, gamma5_out,
                                                           g->geom.V);
-    // w.t now holds the solution in PA precision (t has room: PP >= PA)
-    TSM_TRY(spinor_convert(g, out_prec, x_out, T::PA, w.t.p, nrhs, 0, s));
+    TSM_TRY(spinor_convert(g, out_prec, x_out, T::PP, w.t.p, nrhs, 0, s));
     int bad = 0;
     for (int r = 0; r < nrhs; ++r) {
       const RhsState& h = w.h_st[r];

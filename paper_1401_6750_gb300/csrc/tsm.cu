@@ -49,7 +49,8 @@ struct Accum {
 // Solve sources [first, first + n) with `solver` and add their loops to acc.
 int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho, uint64_t first, int n,
                        int batch, DevBuf& sol, double* acc, Accum& a, cudaStream_t s) {
-  const int op = solver_output_prec(solver);
+  // loops are contracted in FP64 for the all-FP64 solver and in FP32 otherwise
+  const int op = (solver == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
   std::vector<tsm_solve_stats> st(batch);
   for (int k0 = 0; k0 < n; k0 += batch) {
     const int nb = std::min(batch, n - k0);

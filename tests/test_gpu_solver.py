@@ -16,7 +16,7 @@ import pytest
 from conftest import rel_err
 from gpu_helpers import gauge
 from oracle import dirac, lattice, philox, solver
-from paper_1401_6750_gb300 import abi
+from paper_1401_6750_gb300 import abi, api
 
 pytestmark = pytest.mark.gpu
 
@@ -58,7 +58,7 @@ def test_truncated_solvers_meet_rho(ctx, solver_kind, rho, slack, dims):
     u = lattice.effective_links(links, -1)
     n = 5
     nat, stats = g.solve_sources(kappa, mu, solver_kind, rho, seed, 3, n, nrhs_per_launch=2)
-    x = g.unpack(nat, abi.TSM_F32, n).cpu().numpy()
+    x = g.unpack(nat, api.solution_prec(solver_kind), n).cpu().numpy()
     for k in range(n):
         eta = philox.z4_source(dims, seed, 3 + k)
         assert stats[k]["converged"] == 1, stats[k]
@@ -80,7 +80,7 @@ def test_invert_caller_rhs_and_adjoint(ctx):
     u = lattice.effective_links(links, -1)
     b = synth.gaussian_spinor(dims, 10, nrhs=2)
     for solver_kind, prec, tol in ((abi.TSM_SOLVER_F64, abi.TSM_F64, 1e-9),
-                                   (abi.TSM_SOLVER_F32_RELIABLE, abi.TSM_F32, 1e-5)):
+                                   (abi.TSM_SOLVER_F32_RELIABLE, abi.TSM_F64, 1e-9)):
         nb = g.pack(to_device(b), prec)
         for op in (abi.TSM_OP_M, abi.TSM_OP_MDAG):
             nx, st = g.invert(op, kappa, mu, solver_kind, 1e-10, nb, 2)
