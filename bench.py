@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", default=None, choices=["dslash", "tsm"],
                     help="run a few launches of one kernel family for an ncu capture and exit")
+    ap.add_argument("--probe-time", action="store_true", help="with --probe dslash: print event-timed GB/s")
     return ap.parse_args()
 
 
@@ -233,6 +234,10 @@ def probe(args):
         src = g.sources(5, 0, args.nrhs, prec)
         for _ in range(3):
             g.dslash(abi.TSM_OP_M, WORKLOAD["kappa"], WORKLOAD["mu"], prec, src, args.nrhs)
+        if args.probe_time:
+            peak, _ = measured_peak_gbs()
+            for p in (abi.TSM_F16, abi.TSM_BF16, abi.TSM_F32, abi.TSM_F64):
+                print(json.dumps(_dslash_roofline(g, abi, torch, peak, p, args.nrhs)), flush=True)
     else:
         lp = abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16
         g.tsm(WORKLOAD["kappa"], WORKLOAD["mu"], args.nrhs, args.n_hp, WORKLOAD["rho_lp"], WORKLOAD["rho_hp"], lp,

@@ -172,6 +172,7 @@ int tsm_create_gauge(tsm_ctx* ctx, const int dims[4], const double* links_host, 
   for (int d = 0; d < 4; ++d) g->geom.L[d] = dims[d];
   g->geom.V = (int)v;
   g->geom.bc = t_bc;
+  for (int d = 0; d < 3; ++d) g->geom.div[d] = make_fastdiv((uint32_t)dims[d]);
   g->precisions = precisions;
   int rc = build_links(g, links_host);
   if (rc != TSM_OK) {

@@ -65,19 +65,50 @@ template <typename R>
 __device__ __forceinline__ R norm2(cplx<R> a) { return a.re * a.re + a.im * a.im; }
 
 // ---------------------------------------------------------------- geometry
+// Exact unsigned division by an invariant d through multiply and shift
+// (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, for every 32-bit n
+//   t = mulhi(m, n),  n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+  uint32_t d, m, s1, s2;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  FastDiv f;
+  f.d = d;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l > 1 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(f.m, n);
+#else
+  const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Geom {
   int L[4];  // Lx, Ly, Lz, T
   int V;
   int bc;    // temporal boundary sign on the last timeslice
+  FastDiv div[3];  // by Lx, Ly, Lz
 };
 
 __device__ __forceinline__ void site_coords(const Geom& g, int i, int c[4]) {
-  c[0] = i % g.L[0];
-  int r = i / g.L[0];
-  c[1] = r % g.L[1];
-  r /= g.L[1];
-  c[2] = r % g.L[2];
-  c[3] = r / g.L[2];
+  uint32_t q = fast_div((uint32_t)i, g.div[0]);
+  c[0] = i - (int)q * g.L[0];
+  uint32_t q2 = fast_div(q, g.div[1]);
+  c[1] = (int)q - (int)q2 * g.L[1];
+  uint32_t q3 = fast_div(q2, g.div[2]);
+  c[2] = (int)q2 - (int)q3 * g.L[2];
+  c[3] = (int)q3;
 }
 
 // strides of the lexicographic site index

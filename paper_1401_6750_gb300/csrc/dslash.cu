@@ -1,5 +1,7 @@
 // Stand-alone operator applications behind tsm_dslash_tm (Eq. 1's M, M^dag,
 // A and M^dag M) on native fields.
+#include <stdlib.h>
+
 #include "dslash.cuh"
 #include "internal.h"
 
@@ -8,8 +10,8 @@ namespace tsm {
 namespace {
 
 template <typename R, int SF, int PIN, int PL, int PO>
-int launch_store(const tsm_gauge* g, double kappa, double tw, const void* in, void* out, int nrhs, int gamma5,
-                 cudaStream_t s) {
+int launch_store(tsm_gauge* g, double kappa, double tw, const void* in, void* out, int nrhs, int gamma5,
+                 cudaStream_t s, int nr_forced = 0) {
   DslashArgs a;
   a.g = g->geom;
   a.links = g->links[PL].p;
@@ -23,14 +25,16 @@ int launch_store(const tsm_gauge* g, double kappa, double tw, const void* in, vo
   e.V = (size_t)g->geom.V;
   e.gamma5 = gamma5;
   e.red = RedSlots{nullptr, nullptr};
+  int nr = nr_forced;
+  if (nr == 0) TSM_TRY(tuned_nr(g, PIN, PL, nrhs, s, &nr));
   count_launches(1);
-  dslash_kernel<R, SF, PIN, PL, EpiStore<R, PO>><<<dslash_grid(g->geom.V, nrhs), DSLASH_BS, 0, s>>>(a, e);
+  launch_dslash<R, SF, PIN, PL>(nr, a, e, s);
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }
 
 template <int SF>
-int dispatch_store(const tsm_gauge* g, int pf, int pl, double kappa, double tw, const void* in, void* out, int nrhs,
+int dispatch_store(tsm_gauge* g, int pf, int pl, double kappa, double tw, const void* in, void* out, int nrhs,
                    int gamma5, cudaStream_t s) {
   if (pf == TSM_F64 && pl == TSM_F64)
     return launch_store<double, SF, TSM_F64, TSM_F64, TSM_F64>(g, kappa, tw, in, out, nrhs, gamma5, s);
@@ -47,7 +51,82 @@ int dispatch_store(const tsm_gauge* g, int pf, int pl, double kappa, double tw, 
   return fail(TSM_ERR_INVALID_ARG, "no operator for field precision %d with link precision %d", pf, pl);
 }
 
+// Time the plain operator for each candidate of right-hand sides per thread.
+template <typename R, int PIN, int PL>
+int tune(tsm_gauge* g, int nrhs, cudaStream_t s, int* best) {
+  const size_t bytes = (size_t)nrhs * spinor_chunks(PIN) * (size_t)g->geom.V * 16;
+  DevBuf in, out;
+  TSM_TRY(in.reserve(bytes));
+  TSM_TRY(out.reserve(bytes));
+  TSM_CUDA(cudaMemsetAsync(in.p, 0, bytes, s));
+  EventPair ev;
+  float best_t = 1e30f;
+  *best = 1;
+  for (int nr : {1, 2, 4}) {
+    if (nr > nrhs || (sizeof(R) == 8 && nr > 2)) break;
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      TSM_TRY(ev.begin(s));
+      TSM_TRY((launch_store<R, -1, PIN, PL, PIN>(g, 0.1, 0.01, in.p, out.p, nrhs, 0, s, nr)));
+      TSM_TRY(ev.end(s));
+      const float t = (float)ev.seconds();
+      if (rep > 0 && t < tmin) tmin = t;
+    }
+    if (tmin < best_t) {
+      best_t = tmin;
+      *best = nr;
+    }
+  }
+  return TSM_OK;
+}
+
 }  // namespace
+
+int tuned_nr(tsm_gauge* g, int pin, int pl, int nrhs, cudaStream_t s, int* nr) {
+  static const int forced = [] {
+    const char* e = getenv("TSM_DSLASH_NR");
+    return e ? atoi(e) : 0;
+  }();
+  if (forced == 1 || forced == 2 || forced == 4) {
+    *nr = forced;
+    return TSM_OK;
+  }
+  if (nrhs <= 1) {
+    *nr = 1;
+    return TSM_OK;
+  }
+  const long long key = ((long long)pin * 8 + pl) * 100000 + nrhs;
+  {
+    std::lock_guard<std::mutex> l(g->tune_mu);
+    auto it = g->nr_cache.find(key);
+    if (it != g->nr_cache.end()) {
+      *nr = it->second;
+      return TSM_OK;
+    }
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TSM_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {  // cannot time inside a capture: fall back
+    *nr = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+    return TSM_OK;
+  }
+  int best = 1;
+  if (pin == TSM_F64 && pl == TSM_F64) {
+    TSM_TRY((tune<double, TSM_F64, TSM_F64>(g, nrhs, s, &best)));
+  } else if (pin == TSM_F32 && pl == TSM_F32) {
+    TSM_TRY((tune<float, TSM_F32, TSM_F32>(g, nrhs, s, &best)));
+  } else if (pin == TSM_F16 && pl == TSM_F16) {
+    TSM_TRY((tune<float, TSM_F16, TSM_F16>(g, nrhs, s, &best)));
+  } else if (pin == TSM_BF16 && pl == TSM_BF16) {
+    TSM_TRY((tune<float, TSM_BF16, TSM_BF16>(g, nrhs, s, &best)));
+  } else {
+    best = nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1);
+  }
+  std::lock_guard<std::mutex> l(g->tune_mu);
+  g->nr_cache[key] = best;
+  *nr = best;
+  return TSM_OK;
+}
 
 int dslash_apply_mixed(tsm_gauge* g, int pf, int pl, int op, double kappa, double mu, const void* in, void* out,
                        int nrhs, int gamma5, cudaStream_t s) {

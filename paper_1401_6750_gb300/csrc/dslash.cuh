@@ -37,30 +37,109 @@ struct RedSlots {
   unsigned* counter;  // [nrhs], zero between launches
 };
 
-// acc += (1 + S g_MU) W h(psi), W = U (DAG false) or U^dag (DAG true); sgn is
-// the boundary sign of the link.
-template <int MU, int S, bool DAG, typename R>
-__device__ __forceinline__ void hop_dir(cplx<R> (&acc)[12], const cplx<R> (&p)[12], const cplx<R> (&u)[3][3],
-                                        R sgn) {
-  const R s = (R)S;
-  cplx<R> h0[3], h1[3];
+// ---------------------------------------------------------------- projection
+// h = (upper two spins of) (1 + S g_MU) psi for the chiral basis:
+//   MU = x: h0 = p0 - S i p3, h1 = p1 - S i p2      (i s1 = [[0, i], [i, 0]])
+//   MU = y: h0 = p0 - S p3,   h1 = p1 + S p2        (i s2 = [[0, 1], [-1, 0]])
+//   MU = z: h0 = p0 - S i p2, h1 = p1 + S i p3      (i s3 = diag(i, -i))
+//   MU = t: h0 = p0 + S p2,   h1 = p1 + S p3
+template <int MU, int S, typename T, class Add, class Sub, class MulI>
+__device__ __forceinline__ void project_pair(T& h0, T& h1, T p0, T p1, T p2, T p3, Add add, Sub sub, MulI muli) {
+  if (MU == 0) {
+    h0 = S > 0 ? sub(p0, muli(p3)) : add(p0, muli(p3));
+    h1 = S > 0 ? sub(p1, muli(p2)) : add(p1, muli(p2));
+  } else if (MU == 1) {
+    h0 = S > 0 ? sub(p0, p3) : add(p0, p3);
+    h1 = S > 0 ? add(p1, p2) : sub(p1, p2);
+  } else if (MU == 2) {
+    h0 = S > 0 ? sub(p0, muli(p2)) : add(p0, muli(p2));
+    h1 = S > 0 ? add(p1, muli(p3)) : sub(p1, muli(p3));
+  } else {
+    h0 = S > 0 ? add(p0, p2) : sub(p0, p2);
+    h1 = S > 0 ? add(p1, p3) : sub(p1, p3);
+  }
+}
+
+// Load the neighbour spinor of field r at site n and project it: h0, h1 (3 colours each).
+template <int MU, int S, int PIN, typename R>
+struct ProjLoad {
+  __device__ __forceinline__ static void run(cplx<R> (&h0)[3], cplx<R> (&h1)[3], const void* base, size_t V, int r,
+                                             int n) {
+    cplx<R> p[12];
+    SpinorIO<PIN>::load(base, V, r, n, p);
+    auto add = [](cplx<R> a, cplx<R> b) { return a + b; };
+    auto sub = [](cplx<R> a, cplx<R> b) { return a - b; };
+    auto muli = [](cplx<R> a) { return times_i(a); };
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const cplx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
-    if (MU == 0) {          // h = psi_u - S i s1 psi_l
-      h0[c] = p0 - s * times_i(p3);
-      h1[c] = p1 - s * times_i(p2);
-    } else if (MU == 1) {   // i s2 = [[0, 1], [-1, 0]]
-      h0[c] = p0 - s * p3;
-      h1[c] = p1 + s * p2;
-    } else if (MU == 2) {   // i s3 = diag(i, -i)
-      h0[c] = p0 - s * times_i(p2);
-      h1[c] = p1 + s * times_i(p3);
-    } else {                // g_t: h = psi_u + S psi_l
-      h0[c] = p0 + s * p2;
-      h1[c] = p1 + s * p3;
+    for (int c = 0; c < 3; ++c) project_pair<MU, S>(h0[c], h1[c], p[c], p[3 + c], p[6 + c], p[9 + c], add, sub, muli);
+  }
+};
+
+// 16-bit storage: project in packed half2 / bfloat162 arithmetic, widen only h.
+template <bool BF>
+struct Packed2 {
+  __device__ __forceinline__ static uint32_t add(uint32_t a, uint32_t b) {
+    if (BF) {
+      __nv_bfloat162 r = __hadd2(*reinterpret_cast<__nv_bfloat162*>(&a), *reinterpret_cast<__nv_bfloat162*>(&b));
+      return *reinterpret_cast<uint32_t*>(&r);
+    } else {
+      __half2 r = __hadd2(*reinterpret_cast<__half2*>(&a), *reinterpret_cast<__half2*>(&b));
+      return *reinterpret_cast<uint32_t*>(&r);
     }
   }
+  __device__ __forceinline__ static uint32_t sub(uint32_t a, uint32_t b) {
+    if (BF) {
+      __nv_bfloat162 r = __hsub2(*reinterpret_cast<__nv_bfloat162*>(&a), *reinterpret_cast<__nv_bfloat162*>(&b));
+      return *reinterpret_cast<uint32_t*>(&r);
+    } else {
+      __half2 r = __hsub2(*reinterpret_cast<__half2*>(&a), *reinterpret_cast<__half2*>(&b));
+      return *reinterpret_cast<uint32_t*>(&r);
+    }
+  }
+  // i (re, im) = (-im, re): swap the halves, flip the sign bit of the new real part
+  __device__ __forceinline__ static uint32_t muli(uint32_t a) { return __byte_perm(a, 0, 0x1032) ^ 0x00008000u; }
+  __device__ __forceinline__ static float2 widen(uint32_t w) { return BF ? b2f(w) : h2f(w); }
+};
+
+template <int MU, int S, bool BF, typename R>
+__device__ __forceinline__ void proj_load_16(cplx<R> (&h0)[3], cplx<R> (&h1)[3], const void* base, size_t V, int r,
+                                             int n) {
+  const uint4* p = reinterpret_cast<const uint4*>(base) + (size_t)r * 3 * V + n;
+  const uint4 a = __ldg(p), b = __ldg(p + V), c = __ldg(p + 2 * V);
+  const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w};
+  using P2 = Packed2<BF>;
+  auto add = [](uint32_t x, uint32_t y) { return P2::add(x, y); };
+  auto sub = [](uint32_t x, uint32_t y) { return P2::sub(x, y); };
+  auto muli = [](uint32_t x) { return P2::muli(x); };
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    uint32_t q0, q1;
+    project_pair<MU, S>(q0, q1, w[col], w[3 + col], w[6 + col], w[9 + col], add, sub, muli);
+    const float2 f0 = P2::widen(q0), f1 = P2::widen(q1);
+    h0[col] = mk<R>(f0.x, f0.y);
+    h1[col] = mk<R>(f1.x, f1.y);
+  }
+}
+template <int MU, int S, typename R>
+struct ProjLoad<MU, S, TSM_F16, R> {
+  __device__ __forceinline__ static void run(cplx<R> (&h0)[3], cplx<R> (&h1)[3], const void* base, size_t V, int r,
+                                             int n) {
+    proj_load_16<MU, S, false, R>(h0, h1, base, V, r, n);
+  }
+};
+template <int MU, int S, typename R>
+struct ProjLoad<MU, S, TSM_BF16, R> {
+  __device__ __forceinline__ static void run(cplx<R> (&h0)[3], cplx<R> (&h1)[3], const void* base, size_t V, int r,
+                                             int n) {
+    proj_load_16<MU, S, true, R>(h0, h1, base, V, r, n);
+  }
+};
+
+// acc += (1 + S g_MU) W psi given h: w = W h (W = U, or U^dag when DAG), lower spins rebuilt.
+template <int MU, int S, bool DAG, typename R>
+__device__ __forceinline__ void hop_accumulate(cplx<R> (&acc)[12], const cplx<R> (&h0)[3], const cplx<R> (&h1)[3],
+                                               const cplx<R> (&u)[3][3], R sgn) {
+  const R s = (R)S;
   cplx<R> w0[3], w1[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -76,8 +155,10 @@ __device__ __forceinline__ void hop_dir(cplx<R> (&acc)[12], const cplx<R> (&p)[1
         cmac(w1[a], u[a][b], h1[b]);
       }
     }
-    w0[a] = sgn * w0[a];
-    w1[a] = sgn * w1[a];
+    if (MU == 3) {  // only the time direction crosses the boundary
+      w0[a] = sgn * w0[a];
+      w1[a] = sgn * w1[a];
+    }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -99,51 +180,65 @@ __device__ __forceinline__ void hop_dir(cplx<R> (&acc)[12], const cplx<R> (&p)[1
   }
 }
 
-template <int MU, int SF, typename R, int PIN, int PL>
-__device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[12], const DslashArgs& a, int rhs, int i,
-                                            const int c[4]) {
+// Both hops of direction MU for NR right-hand sides r0 .. r0+NR-1 (slots with
+// act[j] false are skipped); each link is loaded and rebuilt once.
+template <int MU, int SF, typename R, int PIN, int PL, int NR>
+__device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[NR][12], const DslashArgs& a, int r0,
+                                            const bool (&act)[NR], int i, const int c[4]) {
   const size_t V = (size_t)a.g.V;
   const int stride = dir_stride(a.g, MU);
-  cplx<R> psi[12];
   cplx<R> u[3][3];
-  // forward: (1 + SF g) U_mu(x) psi(x + mu)
-  {
+  cplx<R> h0[3], h1[3];
+  {  // forward: (1 + SF g) U_mu(x) psi(x + mu)
     const int n = fwd_site(a.g, i, c, MU, stride);
-    SpinorIO<PIN>::load(a.in, V, rhs, n, psi);
     LinkIO<PL>::load(a.links, V, MU, i, u);
     const R sgn = (MU == 3 && c[3] == a.g.L[3] - 1) ? (R)a.g.bc : (R)1;
-    hop_dir<MU, SF, false>(acc, psi, u, sgn);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) continue;
+      ProjLoad<MU, SF, PIN, R>::run(h0, h1, a.in, V, r0 + j, n);
+      hop_accumulate<MU, SF, false>(acc[j], h0, h1, u, sgn);
+    }
   }
-  // backward: (1 - SF g) U_mu(x - mu)^dag psi(x - mu)
-  {
+  {  // backward: (1 - SF g) U_mu(x - mu)^dag psi(x - mu)
     const int n = bwd_site(a.g, i, c, MU, stride);
-    SpinorIO<PIN>::load(a.in, V, rhs, n, psi);
     LinkIO<PL>::load(a.links, V, MU, n, u);
     const R sgn = (MU == 3 && c[3] == 0) ? (R)a.g.bc : (R)1;
-    hop_dir<MU, -SF, true>(acc, psi, u, sgn);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) continue;
+      ProjLoad<MU, -SF, PIN, R>::run(h0, h1, a.in, V, r0 + j, n);
+      hop_accumulate<MU, -SF, true>(acc[j], h0, h1, u, sgn);
+    }
   }
 }
 
-// Full operator at site i: out = in + i tw g5 in - kappa * hop.
-template <int SF, typename R, int PIN, int PL>
-__device__ __forceinline__ void apply_site(cplx<R> (&out)[12], const DslashArgs& a, int rhs, int i) {
+// Full operator at site i for NR right-hand sides: out = in + i tw g5 in - kappa * hop.
+template <int SF, typename R, int PIN, int PL, int NR>
+__device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0, const bool (&act)[NR],
+                                           int i) {
   int c[4];
   site_coords(a.g, i, c);
-  cplx<R> acc[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) acc[k] = mk<R>(0, 0);
-  stencil_dir<0, SF, R, PIN, PL>(acc, a, rhs, i, c);
-  stencil_dir<1, SF, R, PIN, PL>(acc, a, rhs, i, c);
-  stencil_dir<2, SF, R, PIN, PL>(acc, a, rhs, i, c);
-  stencil_dir<3, SF, R, PIN, PL>(acc, a, rhs, i, c);
-  cplx<R> ctr[12];
-  SpinorIO<PIN>::load(a.in, (size_t)a.g.V, rhs, i, ctr);
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[j][k] = mk<R>(0, 0);
+  stencil_dir<0, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  stencil_dir<1, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  stencil_dir<2, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  stencil_dir<3, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
   const R kap = (R)a.kappa, tw = (R)a.tw;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const R g5 = (k < 6) ? (R)1 : (R)-1;
-    cplx<R> t = ctr[k] + (g5 * tw) * times_i(ctr[k]);
-    out[k] = t - kap * acc[k];
+  for (int j = 0; j < NR; ++j) {
+    if (!act[j]) continue;
+    cplx<R> ctr[12];
+    SpinorIO<PIN>::load(a.in, (size_t)a.g.V, r0 + j, i, ctr);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const R g5 = (k < 6) ? (R)1 : (R)-1;
+      cplx<R> t = ctr[k] + (g5 * tw) * times_i(ctr[k]);
+      out[j][k] = t - kap * out[j][k];
+    }
   }
 }
 
@@ -180,20 +275,38 @@ __device__ __forceinline__ void reduce_and_finalize(const Epi& epi, const RedSlo
 //   R site(int rhs, int i, cplx<R>(&out)[12]) -- consume the result, return the value to sum
 //   void finalize(int rhs, double total)      -- last block, thread 0
 //   RedSlots red;
-template <typename R, int SF, int PIN, int PL, class Epi>
+// Grid: blockIdx.x = site_block * ngroups + group, group = NR consecutive right-hand sides.
+template <typename R, int SF, int PIN, int PL, int NR, class Epi>
 __global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi) {
   __shared__ double sh[32];
-  const int rhs = blockIdx.x % a.nrhs;
-  const int blk = blockIdx.x / a.nrhs;
-  if (!epi.active(rhs)) return;
-  const int i = blk * DSLASH_BS + threadIdx.x;
-  R red = (R)0;
-  if (i < a.g.V) {
-    cplx<R> out[12];
-    apply_site<SF, R, PIN, PL>(out, a, rhs, i);
-    red = epi.site(rhs, i, out);
+  const int ngrp = (a.nrhs + NR - 1) / NR;
+  const int grp = blockIdx.x % ngrp;
+  const int blk = blockIdx.x / ngrp;
+  const int r0 = grp * NR;
+  bool act[NR];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    act[j] = (r0 + j < a.nrhs) && epi.active(r0 + j);
+    any |= act[j];
   }
-  if (Epi::kReduce) reduce_and_finalize(epi, epi.red, rhs, a.nblk, blk, (double)red, sh);
+  if (!any) return;
+  const int i = blk * DSLASH_BS + threadIdx.x;
+  R red[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) red[j] = (R)0;
+  if (i < a.g.V) {
+    cplx<R> out[NR][12];
+    apply_site<SF, R, PIN, PL, NR>(out, a, r0, act, i);
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (act[j]) red[j] = epi.site(r0 + j, i, out[j]);
+  }
+  if (Epi::kReduce) {
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (act[j]) reduce_and_finalize(epi, epi.red, r0 + j, a.nblk, blk, (double)red[j], sh);
+  }
 }
 
 // Plain store of the result (optionally times g5), no reduction.
@@ -216,6 +329,25 @@ struct EpiStore {
   __device__ void finalize(int, double) const {}
 };
 
-inline dim3 dslash_grid(int V, int nrhs) { return dim3((unsigned)((V + DSLASH_BS - 1) / DSLASH_BS) * nrhs, 1, 1); }
+inline dim3 dslash_grid(int V, int nrhs, int nr) {
+  return dim3((unsigned)((V + DSLASH_BS - 1) / DSLASH_BS) * (unsigned)((nrhs + nr - 1) / nr), 1, 1);
+}
+
+// Launch with nr right-hand sides per thread (1, 2 or 4; chosen by the autotuner).
+template <typename R, int SF, int PIN, int PL, class Epi>
+inline void launch_dslash(int nr, const DslashArgs& a, const Epi& e, cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (nr == 4) {
+      dslash_kernel<R, SF, PIN, PL, 4, Epi><<<dslash_grid(a.g.V, a.nrhs, 4), DSLASH_BS, 0, s>>>(a, e);
+      return;
+    }
+  }
+  // FP64 sums do not fit 4 right-hand sides in registers: at most 2 there
+  if (nr >= 2) {
+    dslash_kernel<R, SF, PIN, PL, 2, Epi><<<dslash_grid(a.g.V, a.nrhs, 2), DSLASH_BS, 0, s>>>(a, e);
+  } else {
+    dslash_kernel<R, SF, PIN, PL, 1, Epi><<<dslash_grid(a.g.V, a.nrhs, 1), DSLASH_BS, 0, s>>>(a, e);
+  }
+}
 
 }  // namespace tsm

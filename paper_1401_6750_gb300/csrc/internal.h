@@ -97,6 +97,8 @@ struct tsm_gauge {
   std::mutex tsm_mu;       // guards the TSM buffers
   tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
   tsm::DevBuf tsm_sol;     // solutions of one batch
+  std::mutex tune_mu;      // guards nr_cache
+  std::map<long long, int> nr_cache;  // autotuned right-hand sides per thread
   ~tsm_gauge();
 };
 
@@ -108,6 +110,9 @@ inline cudaStream_t pick_stream(const tsm_gauge* g, void* s) {
 inline bool has_prec(const tsm_gauge* g, int p) { return (g->precisions >> p) & 1u; }
 
 // ---- launchers (dslash.cu)
+// Right-hand sides per thread for the stencil on (field precision pin, link
+// precision pl, nrhs), chosen by timing the candidates once per gauge.
+int tuned_nr(tsm_gauge* g, int pin, int pl, int nrhs, cudaStream_t s, int* nr);
 int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
                  cudaStream_t s);
 // out = op in with the link copy `prec_links` (may differ from the field precision `prec_field` only in

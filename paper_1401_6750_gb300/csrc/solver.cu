@@ -403,6 +403,7 @@ struct SolverWorkspace {
   RhsState* h_st = nullptr;
   int* h_mask = nullptr;
   std::map<int, cudaGraphExec_t> graphs;  // chunk graphs per nrhs
+  int nr_s = 1, nr_p = 1;                  // autotuned rhs per thread (sloppy, precise operator)
   double graph_kappa = 0.0, graph_mup = 0.0;
   ~SolverWorkspace() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -510,16 +511,13 @@ struct Solver {
                         const SolveParams& prm, cudaStream_t s) {
     count_launches(3);
     const size_t V = (size_t)g->geom.V;
-    const dim3 grid = dslash_grid(g->geom.V, nrhs);
     {
       EpiMp<Rs, T::PS> e{w.q.p, V, w.st.as<RhsState>(), slots(w)};
-      dslash_kernel<Rs, -1, T::PS, T::PLs, EpiMp<Rs, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup, nrhs), e);
+      launch_dslash<Rs, -1, T::PS, T::PLs>(w.nr_s, args(g, T::PLs, w.p.p, kappa, mup, nrhs), e, s);
     }
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, V, w.st.as<RhsState>(), slots(w), prm};
-      dslash_kernel<Rs, +1, T::PS, T::PLs, EpiCG<Rs, T::PA, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e);
+      launch_dslash<Rs, +1, T::PS, T::PLs>(w.nr_s, args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e, s);
     }
     dim3 eg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 0, g->geom.V);
@@ -534,20 +532,17 @@ struct Solver {
                                 const SolveParams& prm, cudaStream_t s, int n_active) {
     count_launches(3);
     const size_t V = (size_t)g->geom.V;
-    const dim3 grid = dslash_grid(g->geom.V, nrhs);
     EventPair e1, e2, e3;
     TSM_TRY(e1.begin(s));
     {
       EpiMp<Rs, T::PS> e{w.q.p, V, w.st.as<RhsState>(), slots(w)};
-      dslash_kernel<Rs, -1, T::PS, T::PLs, EpiMp<Rs, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.p.p, kappa, mup, nrhs), e);
+      launch_dslash<Rs, -1, T::PS, T::PLs>(w.nr_s, args(g, T::PLs, w.p.p, kappa, mup, nrhs), e, s);
     }
     TSM_TRY(e1.end(s));
     TSM_TRY(e2.begin(s));
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, V, w.st.as<RhsState>(), slots(w), prm};
-      dslash_kernel<Rs, +1, T::PS, T::PLs, EpiCG<Rs, T::PA, T::PS>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e);
+      launch_dslash<Rs, +1, T::PS, T::PLs>(w.nr_s, args(g, T::PLs, w.q.p, kappa, -mup, nrhs), e, s);
     }
     TSM_TRY(e2.end(s));
     TSM_TRY(e3.begin(s));
@@ -604,7 +599,6 @@ struct Solver {
   static int replace_residual(const tsm_gauge* g, SolverWorkspace& w, int nrhs, double kappa, double mup,
                               const SolveParams& prm, cudaStream_t s) {
     const size_t V = (size_t)g->geom.V;
-    const dim3 grid = dslash_grid(g->geom.V, nrhs);
     dim3 eg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
     const void* xsrc = w.x.p;
     count_launches(T::XACC ? 4 : 3);
@@ -614,13 +608,11 @@ struct Solver {
     }
     {
       EpiStoreMasked<Rp, T::PP> e{w.t.p, V, w.mask.as<int>(), RedSlots{nullptr, nullptr}};
-      dslash_kernel<Rp, -1, T::PX, T::PLp, EpiStoreMasked<Rp, T::PP>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, xsrc, kappa, mup, nrhs), e);
+      launch_dslash<Rp, -1, T::PX, T::PLp>(w.nr_p, args(g, T::PLp, xsrc, kappa, mup, nrhs), e, s);
     }
     {
       EpiResidual<Rp, T::PP, T::PA> e{w.b.p, w.r.p, V, w.mask.as<int>(), w.st.as<RhsState>(), slots(w), prm};
-      dslash_kernel<Rp, +1, T::PP, T::PLp, EpiResidual<Rp, T::PP, T::PA>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e);
+      launch_dslash<Rp, +1, T::PP, T::PLp>(w.nr_p, args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e, s);
     }
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 1, g->geom.V);
     TSM_CUDA(cudaGetLastError());
@@ -633,14 +625,23 @@ struct Solver {
     const double mup = 2.0 * kappa * mu;
     const SolveParams prm = params(g, rho, max_iter);
     const size_t V = (size_t)g->geom.V;
-    const dim3 grid = dslash_grid(g->geom.V, nrhs);
+    {
+      int nr_s = 1, nr_p = 1;
+      TSM_TRY(tuned_nr(g, T::PS, T::PLs, nrhs, s, &nr_s));
+      TSM_TRY(tuned_nr(g, T::PP, T::PLp, nrhs, s, &nr_p));
+      if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
+        for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
+        w.graphs.clear();
+      }
+      w.nr_s = nr_s;
+      w.nr_p = nr_p;
+    }
     dim3 eg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
     // b = M^dag eta (precise), state initialisation
     count_launches(2);
     {
       EpiInitB<Rp, T::PP> e{w.b.p, V, w.st.as<RhsState>(), slots(w), prm};
-      dslash_kernel<Rp, +1, T::PP, T::PLp, EpiInitB<Rp, T::PP>>
-          <<<grid, DSLASH_BS, 0, s>>>(args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e);
+      launch_dslash<Rp, +1, T::PP, T::PLp>(w.nr_p, args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e, s);
     }
     k_init<T::PP, T::PA, T::PS, T::XACC>
         <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.as<double2>(), w.st.as<RhsState>(), g->geom.V);
