@@ -182,6 +182,30 @@ int tsm_contract_loops(tsm_gauge* g, double kappa, double mu, int prec,
                        const void* s_dev, int nsrc, int n_mom, const int* mom,
                        double* out_dev, int accumulate, void* stream);
 
+/* Allocation-free variant of tsm_contract_loops (the paper has no
+ * counterpart: it is an interface convenience).  It is meant for callers
+ * that cannot call cudaMalloc during the call -- e.g. code running under a
+ * memory pool or allocator that forbids new device allocations, or latency-
+ * sensitive loops where an allocation would synchronise the device.  The
+ * caller still passes the solutions and the output; the library's own
+ * scratch (g5 A s for every source, the per-plane partial projections and a
+ * copy of the momentum list) lives in a fixed array of
+ * TSM_CONTRACT_NOALLOC_MAX_BYTES compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  Needs
+ *   256-rounded(12 n_mom) + 256-rounded(nsrc * V * 16 * NCH)
+ *   + 256-rounded(Lz * T * 160 * (2R+1)^2 * 16)  bytes  (R = max |n_i|)
+ * and returns TSM_ERR_INVALID_ARG, touching nothing, when that exceeds the
+ * maximum.  The first call on a device looks up the array's device address
+ * and uploads a constant table there (make it before any stream capture);
+ * no call allocates device memory.  All calls share the array and it keeps
+ * the last call's contents: calls that overlap on the GPU (two streams, two
+ * threads) race.  Results equal tsm_contract_loops'. */
+#define TSM_CONTRACT_NOALLOC_MAX_BYTES (32 * 1024 * 1024)
+int tsm_contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec,
+                               const void* s_dev, int nsrc, int n_mom,
+                               const int* mom, double* out_dev, int accumulate,
+                               void* stream);
+
 typedef struct {
   double kappa, mu;
   int n_lp, n_hp;          /* low-precision (bulk) and correction source counts */

@@ -18,6 +18,7 @@ TSM_F64, TSM_F32, TSM_F16, TSM_BF16 = 0, 1, 2, 3
 TSM_OP_M, TSM_OP_MDAG, TSM_OP_A, TSM_OP_MDAGM = 0, 1, 2, 3
 TSM_SOLVER_F64, TSM_SOLVER_F32_RELIABLE, TSM_SOLVER_LP_F16, TSM_SOLVER_LP_BF16 = 0, 1, 2, 3
 TSM_N_INSERTIONS = 160
+TSM_CONTRACT_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 CHUNKS = {TSM_F64: 12, TSM_F32: 6, TSM_F16: 3, TSM_BF16: 3}
 
 
@@ -66,6 +67,8 @@ _SIGNATURES = {
                            ctypes.POINTER(tsm_solve_stats), _P]),
     "tsm_contract_loops": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int, ctypes.POINTER(c_int),
                                    _P, c_int, _P]),
+    "tsm_contract_loops_noalloc": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int,
+                                           ctypes.POINTER(c_int), _P, c_int, _P]),
     "tsm_solve_tsm": (c_int, [_P, ctypes.POINTER(tsm_params), _P, _P, ctypes.POINTER(tsm_stats), _P]),
     "tsm_solve_tsm_dev": (c_int, [_P, ctypes.POINTER(tsm_params), _P, _P, ctypes.POINTER(tsm_stats), _P]),
     "tsm_momentum_table": (c_int, [c_int, ctypes.POINTER(c_int), c_int]),

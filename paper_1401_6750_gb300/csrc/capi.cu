@@ -305,6 +305,22 @@ int tsm_contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const vo
   return contract_loops(g, kappa, mu, prec, s_dev, nsrc, n_mom, mom, out_dev, accumulate, s);
 }
 
+int tsm_contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc,
+                               int n_mom, const int* mom, double* out_dev, int accumulate, void* stream) {
+  if (!g || !s_dev || !out_dev || nsrc < 0 || n_mom < 1 || !mom)
+    return fail(TSM_ERR_INVALID_ARG, "tsm_contract_loops_noalloc: bad argument");
+  if (nsrc > 65535) return fail(TSM_ERR_INVALID_ARG, "nsrc %d > 65535", nsrc);
+  if (!isfinite(kappa) || !isfinite(mu)) return fail(TSM_ERR_INVALID_ARG, "kappa and mu must be finite");
+  TSM_TRY(bind(g));
+  cudaStream_t s = pick_stream(g, stream);
+  if (nsrc == 0) {
+    if (!accumulate)
+      TSM_CUDA(cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * 160 * (size_t)n_mom * g->geom.L[3], s));
+    return TSM_OK;
+  }
+  return contract_loops_noalloc(g, kappa, mu, prec, s_dev, nsrc, n_mom, mom, out_dev, accumulate, s);
+}
+
 int tsm_momentum_table(int p2max, int* out, int cap) {
   std::vector<int> v;
   const int n = momentum_table(p2max, v);

@@ -456,3 +456,88 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
 }
 
 }  // namespace tsm
+
+// ---------------------------------------------------------------- allocation-free variant
+// For callers that must not allocate device memory during a call -- code that
+// runs while a memory pool or a graph capture forbids cudaMalloc, or
+// latency-bound loops where an allocation would synchronise the device --
+// the contraction can run entirely in a fixed scratch region compiled into
+// the library.  Every device that loads the library holds this array until
+// the process exits.  All calls on a device share it, so calls that overlap
+// on the GPU race; nothing in it needs to start at zero (each launch writes
+// every scratch word it later reads).
+static __device__ __align__(256) unsigned char g_contract_scratch[TSM_CONTRACT_NOALLOC_MAX_BYTES];
+
+namespace tsm {
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+// Host-side address of the scratch array on `dev` (which must be current);
+// looked up, together with the Gamma table upload, on the first call per device.
+int noalloc_setup(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(TSM_ERR_INVALID_ARG, "device %d out of range", dev);
+  std::lock_guard<std::mutex> l(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_contract_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
+    GammaTable t;
+    TSM_TRY(build_gamma_table(t));
+    TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+    g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TSM_OK;
+}
+}  // namespace
+
+int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
+                           const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
+  if (prec != TSM_F32 && prec != TSM_F64)
+    return fail(TSM_ERR_INVALID_ARG, "contraction takes F32 or F64 solutions, got precision %d", prec);
+  if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
+  int rad = 0;
+  for (int m = 0; m < n_mom; ++m)
+    for (int d = 0; d < 3; ++d) {
+      const int n = mom_host[3 * m + d];
+      if (n > 8 || n < -8) return fail(TSM_ERR_INVALID_ARG, "momentum component %d outside [-8, 8]", n);
+      rad = std::max(rad, n < 0 ? -n : n);
+    }
+  const int V = g->geom.V;
+  const int nx = 2 * rad + 1;
+  const int lz = g->geom.L[2], lt = g->geom.L[3];
+  const size_t mom_bytes = round256(sizeof(int) * 3 * (size_t)n_mom);
+  const size_t v_bytes = round256((size_t)nsrc * spinor_chunks(prec) * V * 16);
+  const size_t part_bytes = round256((size_t)lz * lt * 160 * nx * nx * sizeof(double2));
+  const size_t need = mom_bytes + v_bytes + part_bytes;
+  if (need > (size_t)TSM_CONTRACT_NOALLOC_MAX_BYTES)
+    return fail(TSM_ERR_INVALID_ARG,
+                "tsm_contract_loops_noalloc needs %zu scratch bytes (fields %zu + partial sums %zu), above the "
+                "fixed %d; use fewer sources per call, a smaller momentum radius or tsm_contract_loops",
+                need, v_bytes, part_bytes, (int)TSM_CONTRACT_NOALLOC_MAX_BYTES);
+  unsigned char* base = nullptr;
+  TSM_TRY(noalloc_setup(g->ctx->device, &base));
+  int* mom_dev = reinterpret_cast<int*>(base);
+  void* v_dev = base + mom_bytes;
+  double2* part = reinterpret_cast<double2*>(base + mom_bytes + v_bytes);
+  TSM_CUDA(cudaMemcpyAsync(mom_dev, mom_host, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, st));
+  TSM_TRY(dslash_apply_fixed(g, prec, TSM_OP_A, kappa, 0.0, s_dev, v_dev, nsrc, 1, 1, st));
+  if (prec == TSM_F32)
+    TSM_TRY((launch_planes<float, TSM_F32, TSM_F32>(g, s_dev, v_dev, nsrc, rad, part, st)));
+  else
+    TSM_TRY((launch_planes<double, TSM_F64, TSM_F64>(g, s_dev, v_dev, nsrc, rad, part, st)));
+  const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
+  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
+  count_launches(1);
+  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(part, mom_dev, n_mom, lz, lt, rad, nx, 2.0 * kappa * mu,
+                                                      out_dev, accumulate);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+}  // namespace tsm

@@ -146,6 +146,19 @@ int dslash_apply_mixed(tsm_gauge* g, int pf, int pl, int op, double kappa, doubl
   return fail(TSM_ERR_INVALID_ARG, "unknown operator %d", op);
 }
 
+int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
+                       int gamma5, int nr, cudaStream_t s) {
+  if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
+  const double mup = 2.0 * kappa * mu;
+  if (op != TSM_OP_A && op != TSM_OP_M) return fail(TSM_ERR_INVALID_ARG, "fixed-shape launch supports M and A only");
+  const double tw = (op == TSM_OP_M) ? mup : 0.0;
+  switch (prec) {
+    case TSM_F64: return launch_store<double, -1, TSM_F64, TSM_F64, TSM_F64>(g, kappa, tw, in, out, nrhs, gamma5, s, nr);
+    case TSM_F32: return launch_store<float, -1, TSM_F32, TSM_F32, TSM_F32>(g, kappa, tw, in, out, nrhs, gamma5, s, nr);
+  }
+  return fail(TSM_ERR_INVALID_ARG, "fixed-shape launch supports F64 and F32 fields");
+}
+
 int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
                  cudaStream_t s) {
   return dslash_apply_mixed(g, prec, prec, op, kappa, mu, in, out, nrhs, 0, s);

@@ -119,6 +119,9 @@ int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const 
 // the combinations instantiated there); gamma5 != 0 stores g5 * result.
 int dslash_apply_mixed(tsm_gauge* g, int prec_field, int prec_links, int op, double kappa, double mu,
                        const void* in, void* out, int nrhs, int gamma5, cudaStream_t s);
+// M or A on F64/F32 fields with a fixed number of right-hand sides per thread (no autotuning, no allocation).
+int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
+                       int gamma5, int nr, cudaStream_t s);
 
 // ---- fields (fields.cu)
 int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* out, cudaStream_t s);
@@ -145,6 +148,8 @@ unsigned solver_link_precs(int solver);
 // ---- contraction (contract.cu)
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                    const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
+int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
+                           const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 
 // ---- misc
 int momentum_table(int p2max, std::vector<int>& out);
