@@ -49,17 +49,19 @@ def bilinear(a, g, b):
     return np.einsum("...sc,sr,...rc->...", np.conj(a), g, b)
 
 
-def loop_densities(u, s, kappa, mu):
-    """Per-site densities of all 160 insertions for one solved source s.
-
-    ``u`` are effective links; ``s`` may carry leading batch axes (several
-    sources).  Returns complex128 (160, ..., t, z, y, x).
-    """
+def loop_densities_pair(u, a, b, kappa, mu, prefactor_derivative=False):
+    """The sesquilinear form behind the loop densities: phi = g5 a on the left,
+    chi_0 = b and chi_1 = g5 A b on the right, so loop_densities(s) is the
+    pair (s, s).  With prefactor_derivative the flavour prefactors are
+    replaced by their mu-derivatives (-2 i mu' -> -4 i kappa, 2 -> 0)."""
     mu_p = 2.0 * kappa * mu
-    phi = dirac.gamma5(s)
-    v = dirac.gamma5(dirac.apply_A(u, s, kappa))
-    out = np.zeros((N_INSERTIONS,) + s.shape[:-2], dtype=np.complex128)
-    for flavour, (chi, pref) in enumerate(((s, -2j * mu_p), (v, 2.0))):
+    phi = dirac.gamma5(a)
+    v = dirac.gamma5(dirac.apply_A(u, b, kappa))
+    prefs = (-4j * kappa, 0.0) if prefactor_derivative else (-2j * mu_p, 2.0)
+    out = np.zeros((N_INSERTIONS,) + a.shape[:-2], dtype=np.complex128)
+    for flavour, (chi, pref) in enumerate(((b, prefs[0]), (v, prefs[1]))):
+        if pref == 0.0:
+            continue
         for g in range(16):
             out[insertion_index(flavour, False, 0, g)] = pref * bilinear(phi, INSERTIONS[g], chi)
         for m in range(4):
@@ -73,6 +75,15 @@ def loop_densities(u, s, kappa, mu):
                 t4 = bilinear(phi, gm, dirac.colour_mul_dag(ub, lattice.bwd(chi, m)))
                 out[insertion_index(flavour, True, m, g)] = pref * 0.25 * (t1 - t2 + t3 - t4)
     return out
+
+
+def loop_densities(u, s, kappa, mu):
+    """Per-site densities of all 160 insertions for one solved source s.
+
+    ``u`` are effective links; ``s`` may carry leading batch axes (several
+    sources).  Returns complex128 (160, ..., t, z, y, x).
+    """
+    return loop_densities_pair(u, s, s, kappa, mu)
 
 
 def phases(dims, moms):

@@ -60,7 +60,8 @@ struct Traits<TSM_SOLVER_F32_RELIABLE> {
   using Rp = double;
   static constexpr int PS = TSM_F32, PA = TSM_F32, PP = TSM_F64, PLs = TSM_F32, PLp = TSM_F64, PX = TSM_F64;
   static constexpr bool XACC = true, SCALED = false;
-  static constexpr double DELTA = 0.1;
+  // FP32 recurrences stay accurate over three decades below the last true residual
+  static constexpr double DELTA = 1e-3;
 };
 template <>
 struct Traits<TSM_SOLVER_LP_F16> {
@@ -496,10 +497,21 @@ struct Solver {
 
   static RedSlots slots(SolverWorkspace& w) { return RedSlots{w.partial.as<double>(), w.counter.as<unsigned>()}; }
 
+  static double delta() {
+    // TSM_RU_DELTA_<kind> overrides the residual-replacement threshold (measurement only)
+    static const double d = [] {
+      char name[32];
+      snprintf(name, sizeof(name), "TSM_RU_DELTA_%d", KIND);
+      const char* e = getenv(name);
+      return e ? atof(e) : T::DELTA;
+    }();
+    return d;
+  }
+
   static SolveParams params(const tsm_gauge* g, double rho, int max_iter) {
     SolveParams p;
     p.rho2 = rho * rho;
-    p.delta2 = T::DELTA * T::DELTA;
+    p.delta2 = delta() * delta();
     p.inv_ncomp = 1.0 / (12.0 * (double)g->geom.V);
     p.max_iter = max_iter;
     p.scaled = T::SCALED ? 1 : 0;
