@@ -182,6 +182,23 @@ int tsm_contract_loops(tsm_gauge* g, double kappa, double mu, int prec,
                        const void* s_dev, int nsrc, int n_mom, const int* mom,
                        double* out_dev, int accumulate, void* stream);
 
+/* Backward of the loops for automatic differentiation (used by the PyTorch
+ * autograd wrapper; the derivatives of Sec. 2.1.1's loops with respect to
+ * the twisted mass and the sources, by the adjoint method through Eq. 1).
+ * Given the solutions s_r = M(mu)^{-1} eta_r (native, prec F64 or F32, nsrc
+ * fields) used to form the loops L = sum_r [tsm_contract_loops of s_r] on the
+ * momenta mom, and grad_dev = dl/dRe L + i dl/dIm L for a real loss l
+ * (device doubles [160][n_mom][T][2]), this computes
+ *   *dmu_host   = dl/dmu   (through s and the explicit mu' of the tau_3 loops)
+ *   grad_eta_dev (optional, native prec, nsrc fields) = dl/dRe eta + i dl/dIm eta
+ * with one adjoint solve lambda_r = M^{-dag} g_r per source, by `solver`
+ * (TSM_SOLVER_F64 or TSM_SOLVER_F32_RELIABLE) to `rho`.  Synchronises. */
+int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec,
+                       const void* s_dev, int nsrc, int n_mom, const int* mom,
+                       const double* grad_dev, int solver, double rho,
+                       int max_iter, double* dmu_host, void* grad_eta_dev,
+                       void* stream);
+
 /* Allocation-free variant of tsm_contract_loops (the paper has no
  * counterpart: it is an interface convenience).  It is meant for callers
  * that cannot call cudaMalloc during the call -- e.g. code running under a

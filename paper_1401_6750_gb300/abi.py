@@ -67,6 +67,8 @@ _SIGNATURES = {
                            ctypes.POINTER(tsm_solve_stats), _P]),
     "tsm_contract_loops": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int, ctypes.POINTER(c_int),
                                    _P, c_int, _P]),
+    "tsm_loops_backward": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int, ctypes.POINTER(c_int), _P,
+                                   c_int, c_double, c_int, ctypes.POINTER(c_double), _P, _P]),
     "tsm_contract_loops_noalloc": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int,
                                            ctypes.POINTER(c_int), _P, c_int, _P]),
     "tsm_solve_tsm": (c_int, [_P, ctypes.POINTER(tsm_params), _P, _P, ctypes.POINTER(tsm_stats), _P]),

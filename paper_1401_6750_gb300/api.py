@@ -167,3 +167,53 @@ def loops_complex(out):
     """[160][n_mom][T][2] float64 tensor -> complex128 numpy array."""
     a = out.detach().cpu().numpy()
     return a[..., 0] + 1j * a[..., 1]
+
+
+class OneEndLoops(torch.autograd.Function):
+    """Differentiable one-end loops (Sec. 2.1.1) of caller sources.
+
+    forward(mu, eta): s = M(mu)^{-1} eta by `solver` (tsm_invert), loops of
+    all 160 insertions on `moms` summed over the sources (tsm_contract_loops,
+    in `prec`), returned as complex128 (160, n_mom, T).
+    backward: tsm_loops_backward (adjoint solve with M^dag) -> dl/dmu and
+    dl/deta.  mu is a 0-d float64 tensor, eta complex128 (nsrc, T, Lz, Ly, Lx, 4, 3).
+    """
+
+    @staticmethod
+    def forward(ctx, mu, eta, gauge, kappa, moms, solver, rho, prec, max_iter):
+        mu_v = float(mu)
+        nsrc = eta.shape[0]
+        b = gauge.pack(eta.detach(), solution_prec(solver))
+        s, _ = gauge.invert(abi.TSM_OP_M, kappa, mu_v, solver, rho, b, nsrc, max_iter=max_iter)
+        if prec != solution_prec(solver):
+            s = gauge.pack(gauge.unpack(s, solution_prec(solver), nsrc), prec)
+        out = gauge.contract(kappa, mu_v, prec, s, nsrc, moms)
+        ctx.gauge, ctx.kappa, ctx.mu, ctx.solver, ctx.rho, ctx.prec = gauge, kappa, mu_v, solver, rho, prec
+        ctx.max_iter, ctx.nsrc, ctx.s = max_iter, nsrc, s
+        ctx.moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        ctx.mu_meta = (mu.dtype, mu.device)
+        ctx.eta_meta = (eta.dtype, eta.device)
+        return torch.view_as_complex(out.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_loops):
+        g = ctx.gauge
+        gd = torch.view_as_real(grad_loops.to(device="cuda", dtype=torch.complex128).contiguous()).contiguous()
+        dmu = ctypes.c_double()
+        grad_eta = g.empty_native(ctx.prec, ctx.nsrc) if ctx.needs_input_grad[1] else None
+        mom_c = ctx.moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        abi.check(abi.lib().tsm_loops_backward(g.handle, ctx.kappa, ctx.mu, ctx.prec, _ptr(ctx.s), ctx.nsrc,
+                                               ctx.moms.shape[0], mom_c, _ptr(gd), ctx.solver, ctx.rho,
+                                               ctx.max_iter, ctypes.byref(dmu),
+                                               _ptr(grad_eta) if grad_eta is not None else None, _stream()),
+                  "tsm_loops_backward")
+        dmu_t = torch.tensor(dmu.value, dtype=ctx.mu_meta[0], device=ctx.mu_meta[1])
+        geta = None
+        if grad_eta is not None:
+            geta = g.unpack(grad_eta, ctx.prec, ctx.nsrc).to(dtype=ctx.eta_meta[0], device=ctx.eta_meta[1])
+        return dmu_t, geta, None, None, None, None, None, None, None
+
+
+def one_end_loops(mu, eta, gauge, kappa, moms, solver=abi.TSM_SOLVER_F64, rho=1e-12, prec=abi.TSM_F64,
+                  max_iter=100000):
+    return OneEndLoops.apply(mu, eta, gauge, kappa, moms, solver, rho, prec, max_iter)

@@ -321,6 +321,24 @@ int tsm_contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, 
   return contract_loops_noalloc(g, kappa, mu, prec, s_dev, nsrc, n_mom, mom, out_dev, accumulate, s);
 }
 
+int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
+                       const int* mom, const double* grad_dev, int solver, double rho, int max_iter, double* dmu_host,
+                       void* grad_eta_dev, void* stream) {
+  if (!g || !s_dev || !grad_dev || !dmu_host || nsrc < 1 || n_mom < 1 || !mom)
+    return fail(TSM_ERR_INVALID_ARG, "tsm_loops_backward: bad argument");
+  if (prec != TSM_F64 && prec != TSM_F32) return fail(TSM_ERR_INVALID_ARG, "solutions must be F64 or F32");
+  if (solver != TSM_SOLVER_F64 && solver != TSM_SOLVER_F32_RELIABLE)
+    return fail(TSM_ERR_INVALID_ARG, "the adjoint solve needs TSM_SOLVER_F64 or TSM_SOLVER_F32_RELIABLE");
+  TSM_TRY(check_solver_args(g, kappa, mu, solver, rho, max_iter));
+  if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
+  if (nsrc > 1024) return fail(TSM_ERR_INVALID_ARG, "at most 1024 sources");
+  for (int m = 0; m < 3 * n_mom; ++m)
+    if (mom[m] > 8 || mom[m] < -8) return fail(TSM_ERR_INVALID_ARG, "momentum component outside [-8, 8]");
+  TSM_TRY(bind(g));
+  return loops_backward(g, kappa, mu, prec, s_dev, nsrc, n_mom, mom, grad_dev, solver, rho, max_iter, dmu_host,
+                        grad_eta_dev, pick_stream(g, stream));
+}
+
 int tsm_momentum_table(int p2max, int* out, int cap) {
   std::vector<int> v;
   const int n = momentum_table(p2max, v);

@@ -76,6 +76,10 @@ struct SolverWsDeleter {
 struct ContractWsDeleter {
   void operator()(ContractWorkspace* w) const;  // contract.cu
 };
+struct GradWorkspace;  // grad.cu
+struct GradWsDeleter {
+  void operator()(GradWorkspace* w) const;  // grad.cu
+};
 
 }  // namespace tsm
 
@@ -97,6 +101,8 @@ struct tsm_gauge {
   std::mutex tsm_mu;       // guards the TSM buffers
   tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
   tsm::DevBuf tsm_sol;     // solutions of one batch
+  std::mutex grad_mu;      // guards grad_ws
+  std::unique_ptr<tsm::GradWorkspace, tsm::GradWsDeleter> grad_ws;
   std::mutex tune_mu;      // guards nr_cache
   std::map<long long, int> nr_cache;  // autotuned right-hand sides per thread
   ~tsm_gauge();
@@ -150,6 +156,11 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
                    const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                            const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
+
+// ---- loop backward (grad.cu)
+int loops_backward(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
+                   const int* mom, const double* grad_dev, int solver, double rho, int max_iter, double* dmu_host,
+                   void* grad_eta_dev, cudaStream_t s);
 
 // ---- misc
 int momentum_table(int p2max, std::vector<int>& out);
