@@ -156,6 +156,26 @@ int tsm_solve_sources(tsm_gauge* g, double kappa, double mu, int solver,
                       uint64_t first_src, int nsrc, int nrhs_per_launch,
                       void* s_dev, tsm_solve_stats* stats_host, void* stream);
 
+/* One instance of an uneven batch: its own gauge field (lattice), twisted
+ * mass and Z4 sources r = first_src .. first_src + nsrc - 1. */
+typedef struct {
+  tsm_gauge* gauge;
+  double kappa, mu;
+  uint64_t noise_seed, first_src;
+  int nsrc;
+  void* s_dev;                  /* out: nsrc solutions, native, solver output precision */
+  tsm_solve_stats* stats_host;  /* optional: nsrc records */
+} tsm_batch_item;
+
+/* Solve every instance of an uneven batch together: each CG kernel is ONE
+ * launch over all instances (lattices of different sizes, different twisted
+ * masses), with a convergence flag per right-hand side; an instance is done
+ * when all its right-hand sides are.  Same solvers, stopping rule and
+ * results as tsm_solve_sources on each instance alone.  All gauges must live
+ * in contexts of the same device.  Allocates its workspace per call. */
+int tsm_solve_batch(tsm_batch_item* items, int n_items, int solver, double rho,
+                    int max_iter, void* stream);
+
 /* Solve op x = b for caller right-hand sides, op = TSM_OP_M (M x = b) or
  * TSM_OP_MDAG (M^dag x = b, through M^dag = g5 M(-mu) g5).  b and x in the
  * native layout of the solver's output precision (F64 for TSM_SOLVER_F64 and

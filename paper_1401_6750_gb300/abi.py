@@ -45,6 +45,12 @@ class tsm_stats(ctypes.Structure):
                 ("n_not_converged", c_int), ("seconds", c_double)]
 
 
+class tsm_batch_item(ctypes.Structure):
+    _fields_ = [("gauge", c_void_p), ("kappa", c_double), ("mu", c_double), ("noise_seed", c_uint64),
+                ("first_src", c_uint64), ("nsrc", c_int), ("s_dev", c_void_p),
+                ("stats_host", ctypes.POINTER(tsm_solve_stats))]
+
+
 class tsm_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_longlong), ("seconds", c_double),
                 ("bytes", c_double), ("flops", c_double)]
@@ -63,6 +69,7 @@ _SIGNATURES = {
     "tsm_make_sources": (c_int, [_P, c_uint64, c_uint64, c_int, c_int, _P, _P]),
     "tsm_solve_sources": (c_int, [_P, c_double, c_double, c_int, c_double, c_int, c_uint64, c_uint64,
                                   c_int, c_int, _P, ctypes.POINTER(tsm_solve_stats), _P]),
+    "tsm_solve_batch": (c_int, [ctypes.POINTER(tsm_batch_item), c_int, c_int, c_double, c_int, _P]),
     "tsm_invert": (c_int, [_P, c_double, c_double, c_int, c_int, c_double, c_int, _P, _P, c_int,
                            ctypes.POINTER(tsm_solve_stats), _P]),
     "tsm_contract_loops": (c_int, [_P, c_double, c_double, c_int, _P, c_int, c_int, ctypes.POINTER(c_int),

@@ -156,6 +156,27 @@ class Gauge:
         return out, stats
 
 
+def solve_batch(instances, solver, rho, max_iter=100000, stream=None, allow_not_converged=False):
+    """Uneven batch in one launch per CG kernel.  instances: list of dicts with
+    keys gauge, kappa, mu, noise_seed, first_src, nsrc.  Returns a list of
+    (solutions native tensor, stats list) per instance."""
+    n = len(instances)
+    items = (abi.tsm_batch_item * n)()
+    outs, stats = [], []
+    for k, inst in enumerate(instances):
+        g = inst["gauge"]
+        out = g.empty_native(solution_prec(solver), inst["nsrc"])
+        st = (abi.tsm_solve_stats * inst["nsrc"])()
+        items[k] = abi.tsm_batch_item(g.handle.value, inst["kappa"], inst["mu"], inst["noise_seed"],
+                                      inst["first_src"], inst["nsrc"], out.data_ptr(),
+                                      ctypes.cast(st, ctypes.POINTER(abi.tsm_solve_stats)))
+        outs.append(out)
+        stats.append(st)
+    rc = abi.lib().tsm_solve_batch(items, n, solver, rho, max_iter, _stream(stream))
+    abi.check(rc, "tsm_solve_batch", (abi.TSM_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return [(o, [dict((f, getattr(x, f)) for f, _ in x._fields_) for x in st]) for o, st in zip(outs, stats)]
+
+
 def momentum_table(p2max=9):
     n = abi.lib().tsm_momentum_table(p2max, None, 0)
     buf = (ctypes.c_int * (3 * n))()

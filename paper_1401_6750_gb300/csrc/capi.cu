@@ -274,6 +274,22 @@ int tsm_solve_sources(tsm_gauge* g, double kappa, double mu, int solver, double 
   return TSM_OK;
 }
 
+int tsm_solve_batch(tsm_batch_item* items, int n_items, int solver, double rho, int max_iter, void* stream) {
+  if (!items || n_items < 1 || n_items > 64) return fail(TSM_ERR_INVALID_ARG, "need 1 to 64 batch items");
+  long long rhs = 0;
+  for (int k = 0; k < n_items; ++k) {
+    const tsm_batch_item& it = items[k];
+    TSM_TRY(check_solver_args(it.gauge, it.kappa, it.mu, solver, rho, max_iter));
+    if (!it.s_dev || it.nsrc < 1 || it.nsrc > 1024) return fail(TSM_ERR_INVALID_ARG, "item %d: bad output or count", k);
+    if (it.gauge->ctx->device != items[0].gauge->ctx->device)
+      return fail(TSM_ERR_INVALID_ARG, "item %d lives on another device", k);
+    rhs += it.nsrc;
+  }
+  if (rhs > 65536) return fail(TSM_ERR_INVALID_ARG, "at most 65536 right-hand sides per batch");
+  TSM_TRY(bind(items[0].gauge));
+  return solve_batch_multi(items, n_items, solver, rho, max_iter, pick_stream(items[0].gauge, stream));
+}
+
 int tsm_invert(tsm_gauge* g, double kappa, double mu, int op, int solver, double rho, int max_iter,
                const void* b_dev, void* x_dev, int nrhs, tsm_solve_stats* stats_host, void* stream) {
   TSM_TRY(check_solver_args(g, kappa, mu, solver, rho, max_iter));

@@ -275,13 +275,15 @@ __device__ __forceinline__ void reduce_and_finalize(const Epi& epi, const RedSlo
 //   R site(int rhs, int i, cplx<R>(&out)[12]) -- consume the result, return the value to sum
 //   void finalize(int rhs, double total)      -- last block, thread 0
 //   RedSlots red;
-// Grid: blockIdx.x = site_block * ngroups + group, group = NR consecutive right-hand sides.
+// One block of work: bid = site_block * ngroups + group, group = NR
+// consecutive right-hand sides.  Shared by the single-instance kernel below
+// and the multi-instance kernels of the batched solver.
 template <typename R, int SF, int PIN, int PL, int NR, class Epi>
-__global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi) {
+__device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi, int bid) {
   __shared__ double sh[32];
   const int ngrp = (a.nrhs + NR - 1) / NR;
-  const int grp = blockIdx.x % ngrp;
-  const int blk = blockIdx.x / ngrp;
+  const int grp = bid % ngrp;
+  const int blk = bid / ngrp;
   const int r0 = grp * NR;
   bool act[NR];
   bool any = false;
@@ -307,6 +309,11 @@ __global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi
     for (int j = 0; j < NR; ++j)
       if (act[j]) reduce_and_finalize(epi, epi.red, r0 + j, a.nblk, blk, (double)red[j], sh);
   }
+}
+
+template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+__global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi) {
+  dslash_block<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
 }
 
 // Plain store of the result (optionally times g5), no reduction.

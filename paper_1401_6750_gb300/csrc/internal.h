@@ -148,6 +148,7 @@ int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double r
                      const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
                      int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
 int solver_precise_prec(int solver);
+int solve_batch_multi(tsm_batch_item* items, int n, int solver, double rho, int max_iter, cudaStream_t s);
 int solver_output_prec(int solver);
 unsigned solver_link_precs(int solver);
 
