@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,T (default 24,24,24,48)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-equal-accuracy", action="store_true")
     ap.add_argument("--probe", default=None, choices=["dslash", "tsm"],
                     help="run a few launches of one kernel family for an ncu capture and exit")
     ap.add_argument("--probe-time", action="store_true", help="with --probe dslash: print event-timed GB/s")
@@ -247,6 +248,72 @@ def probe(args):
     ctx.close()
 
 
+def equal_accuracy(g, abi, torch, w, lp_solver, n_lp=64, n_hp=8, nrhs=32):
+    """TSM against the plain high-precision path at equal final loop accuracy.
+
+    Per-source samples (the scalar and gamma_5 loops of both flavour
+    structures at p = 0, summed over timeslices) give the variances of
+    the LP estimate, the correction L_HP - L_LP and the plain HP estimate;
+    with the measured per-source times the cost to reach a given error is
+      plain: sigma_HP^2 / eps^2 x t_HP
+      TSM:   N_LP t_LP + N_HP (t_HP + t_LP), with sigma_LP^2/N_LP + sigma_corr^2/N_HP = eps^2
+    and the TSM optimum N_LP/N_HP = sqrt(sigma_LP^2 (t_HP + t_LP) / (sigma_corr^2 t_LP)).
+    """
+    import ctypes
+
+    import numpy as np
+    seed = 424242
+    sel = [0, 15, 80, 95]
+    mom = [(0, 0, 0)]
+
+    def per_source(solver, first, n):
+        stream = torch.cuda.current_stream()
+        prec = abi.TSM_F64 if solver in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+        t = 0.0
+        vals = []
+        for k0 in range(0, n, nrhs):
+            m = min(nrhs, n - k0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sol, _ = g.solve_sources(w["kappa"], w["mu"], solver, w["rho_lp"] if solver == lp_solver else w["rho_hp"],
+                                     seed, first + k0, m, nrhs_per_launch=m)
+            e1.record(stream)
+            e1.synchronize()
+            t += e0.elapsed_time(e1) * 1e-3
+            if prec == abi.TSM_F64:  # contract in FP32 like the TSM driver
+                sol = g.pack(g.unpack(sol, abi.TSM_F64, m), abi.TSM_F32)
+            field = g.native_bytes(abi.TSM_F32, 1)
+            for j in range(m):
+                out = g.contract(w["kappa"], w["mu"], abi.TSM_F32, sol[j * field:(j + 1) * field], 1, mom)
+                a = out.cpu().numpy()
+                vals.append((a[sel, 0, :, 0] + 1j * a[sel, 0, :, 1]).sum(axis=1))
+        return np.array(vals), t / n
+
+    lp_bulk, t_lp = per_source(lp_solver, 0, n_lp)
+    hp, t_hp = per_source(abi.TSM_SOLVER_F32_RELIABLE, n_lp, n_hp)
+    lp_corr, _ = per_source(lp_solver, n_lp, n_hp)
+
+    def var(a):  # real and imaginary parts, per observable
+        return a.real.var(axis=0, ddof=1) + a.imag.var(axis=0, ddof=1)
+
+    s_lp, s_corr, s_hp = var(lp_bulk), var(hp - lp_corr), var(hp)
+    out = []
+    for k, name in enumerate(["scalar tau3", "gamma5 tau3", "scalar", "gamma5"]):
+        if s_hp[k] <= 0:
+            continue
+        ratio = np.sqrt(s_lp[k] * (t_hp + t_lp) / max(s_corr[k] * t_lp, 1e-300))
+        # cost per unit inverse variance: plain s_hp t_hp; TSM (s_lp + s_corr/r)(t_lp + (t_hp+t_lp)/r)
+        cost_plain = s_hp[k] * t_hp
+        cost_tsm = (s_lp[k] + s_corr[k] / ratio) * (t_lp + (t_hp + t_lp) / ratio)
+        out.append({"observable": name, "var_lp": float(s_lp[k]), "var_corr": float(s_corr[k]),
+                    "var_hp": float(s_hp[k]), "opt_lp_per_hp": float(ratio),
+                    "speedup_at_equal_error": float(cost_plain / cost_tsm)})
+    return {"samples": {"lp": n_lp, "hp": n_hp}, "t_lp_s_per_source": t_lp, "t_hp_s_per_source": t_hp,
+            "plain_hp_sources_per_s": 1.0 / t_hp, "observables": out,
+            "note": "p = 0 loops summed over timeslices; variances from per-source samples"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -319,12 +386,8 @@ def main():
             torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        from paper_1401_6750_gb300 import replicas
+        return replicas.max_over_ranks(x, device="cuda")
 
     for k in range(args.warmup):
         step_dev(k)
@@ -390,6 +453,10 @@ def main():
     dslash = [_dslash_roofline(g, abi, torch, peak, abi.TSM_F16, 1),
               _dslash_roofline(g, abi, torch, peak, abi.TSM_F16, 12)]
 
+    eq = None
+    if rank == 0 and not args.no_equal_accuracy:
+        eq = equal_accuracy(g, abi, torch, w, lp_solver)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(dims, w["kappa"], w["mu"], max(lp_iters, 1.0), n_mom)
@@ -415,6 +482,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
             "cpu_baseline": cpu,
+            "equal_accuracy": eq,
         }
         print(json.dumps(line), flush=True)
     g.close()
