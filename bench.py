@@ -225,6 +225,7 @@ def probe(args):
     import torch
     from paper_1401_6750_gb300 import abi, api, build, synth
     build.build()
+    torch.cuda.set_stream(torch.cuda.Stream())  # launches and events on one non-default stream
     dims = [int(v) for v in args.dims.split(",")] if args.dims else WORKLOAD["dims"]
     links = synth.gauge_links(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
     ctx = api.Context(0)

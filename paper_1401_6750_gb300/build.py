@@ -50,7 +50,10 @@ def _digest(extra_flags):
     return h.hexdigest()
 
 
-def build(verbose=False, force=False, extra_flags=(), jobs=None):
+def build(verbose=False, force=False, extra_flags=None, jobs=None):
+    # TSM_NVCC_FLAGS adds compile definitions (variant builds for measurements)
+    if extra_flags is None:
+        extra_flags = os.environ.get("TSM_NVCC_FLAGS", "").split()
     extra_flags = list(extra_flags)
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)

@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(DSLASH_BS) multi_dslash(const InstDesc* __rest
   a.in = mk.in(I);
   a.nblk = I.nblk;
   a.nrhs = I.nrhs;
-  a.kappa = I.kappa;
-  a.tw = mk.tw(I);
+  set_coeffs(a, I.kappa, mk.tw(I));
   dslash_block<R, SF, PIN, PL, 1>(a, mk.epi(I), blockIdx.x - I.dblock0);
 }
 

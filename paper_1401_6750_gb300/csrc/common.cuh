@@ -272,24 +272,39 @@ struct LinkIO<TSM_F32> {
   }
 };
 
+// 16-bit links: two rows kept (12 reals, row 2 rebuilt) unless TSM_LINK16_FULL
+// is defined, in which case all 18 reals are stored:
+//   12-real: [4][V] uint4 (U00 U01 U02 U10), then [4][V] uint2 (U11 U12)
+//   18-real: [4][V] uint4 (U00 U01 U02 U10), [4][V] uint4 (U11 U12 U20 U21), [4][V] uint32 (U22)
 template <bool BF>
 struct Link16IO {
   __device__ __forceinline__ static float2 cvt(uint32_t w) { return BF ? b2f(w) : h2f(w); }
   template <typename R>
   __device__ __forceinline__ static void load(const void* base, size_t V, int mu, int i, cplx<R> (&u)[3][3]) {
     const uint4* pa = reinterpret_cast<const uint4*>(base) + (size_t)mu * V + i;
-    const uint2* pb = reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(base) + 4 * V) +
-                      (size_t)mu * V + i;
     uint4 a = __ldg(pa);
-    uint2 b = __ldg(pb);
     float2 t;
     t = cvt(a.x); u[0][0] = mk<R>(t.x, t.y);
     t = cvt(a.y); u[0][1] = mk<R>(t.x, t.y);
     t = cvt(a.z); u[0][2] = mk<R>(t.x, t.y);
     t = cvt(a.w); u[1][0] = mk<R>(t.x, t.y);
+#ifdef TSM_LINK16_FULL
+    const uint4 b = __ldg(reinterpret_cast<const uint4*>(base) + 4 * V + (size_t)mu * V + i);
+    const uint32_t c = __ldg(reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint4*>(base) + 8 * V) +
+                             (size_t)mu * V + i);
+    t = cvt(b.x); u[1][1] = mk<R>(t.x, t.y);
+    t = cvt(b.y); u[1][2] = mk<R>(t.x, t.y);
+    t = cvt(b.z); u[2][0] = mk<R>(t.x, t.y);
+    t = cvt(b.w); u[2][1] = mk<R>(t.x, t.y);
+    t = cvt(c); u[2][2] = mk<R>(t.x, t.y);
+#else
+    const uint2* pb = reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(base) + 4 * V) +
+                      (size_t)mu * V + i;
+    uint2 b = __ldg(pb);
     t = cvt(b.x); u[1][1] = mk<R>(t.x, t.y);
     t = cvt(b.y); u[1][2] = mk<R>(t.x, t.y);
     reconstruct_row2(u);
+#endif
   }
 };
 template <>
@@ -302,7 +317,11 @@ inline size_t link_bytes(int p, size_t V) {
   switch (p) {
     case TSM_F64: return 4 * 9 * V * 16;
     case TSM_F32: return 4 * 3 * V * 16;
+#ifdef TSM_LINK16_FULL
+    default: return 4 * V * 16 * 2 + 4 * V * 4;
+#else
     default: return 4 * V * 16 + 4 * V * 8;
+#endif
   }
 }
 

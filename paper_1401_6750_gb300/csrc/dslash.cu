@@ -18,8 +18,7 @@ int launch_store(tsm_gauge* g, double kappa, double tw, const void* in, void* ou
   a.in = in;
   a.nblk = (g->geom.V + DSLASH_BS - 1) / DSLASH_BS;
   a.nrhs = nrhs;
-  a.kappa = kappa;
-  a.tw = tw;
+  set_coeffs(a, kappa, tw);
   EpiStore<R, PO> e;
   e.out = out;
   e.V = (size_t)g->geom.V;

@@ -22,6 +22,18 @@ namespace tsm {
 
 constexpr int DSLASH_BS = 128;
 
+// Resident blocks per SM the register allocation must allow (__launch_bounds__):
+// FP32 fields measured fastest at 6 (<= 80 registers); the other kernels keep
+// the compiler's choice.
+template <int PIN>
+struct MinBlocks {
+#ifdef TSM_DSLASH_MINB
+  static constexpr int value = TSM_DSLASH_MINB;
+#else
+  static constexpr int value = (PIN == TSM_F32) ? 6 : 1;
+#endif
+};
+
 struct DslashArgs {
   Geom g;
   const void* links;  // device links in the kernel's link precision
@@ -30,7 +42,28 @@ struct DslashArgs {
   int nrhs;           // right-hand sides in the launch
   double kappa;
   double tw;          // twist coefficient multiplying i g5
+  float kappa_f, tw_f;  // the same, pre-rounded for FP32 kernels (no per-thread FP64 conversion)
 };
+
+template <typename R>
+__device__ __forceinline__ R arg_kappa(const DslashArgs& a);
+template <>
+__device__ __forceinline__ float arg_kappa<float>(const DslashArgs& a) { return a.kappa_f; }
+template <>
+__device__ __forceinline__ double arg_kappa<double>(const DslashArgs& a) { return a.kappa; }
+template <typename R>
+__device__ __forceinline__ R arg_tw(const DslashArgs& a);
+template <>
+__device__ __forceinline__ float arg_tw<float>(const DslashArgs& a) { return a.tw_f; }
+template <>
+__device__ __forceinline__ double arg_tw<double>(const DslashArgs& a) { return a.tw; }
+
+__host__ __device__ inline void set_coeffs(DslashArgs& a, double kappa, double tw) {
+  a.kappa = kappa;
+  a.tw = tw;
+  a.kappa_f = (float)kappa;
+  a.tw_f = (float)tw;
+}
 
 struct RedSlots {
   double* partial;    // [nrhs][nblk]
@@ -227,7 +260,7 @@ __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashA
   stencil_dir<1, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
   stencil_dir<2, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
   stencil_dir<3, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
-  const R kap = (R)a.kappa, tw = (R)a.tw;
+  const R kap = arg_kappa<R>(a), tw = arg_tw<R>(a);
 #pragma unroll
   for (int j = 0; j < NR; ++j) {
     if (!act[j]) continue;
@@ -312,7 +345,7 @@ __device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi
 }
 
 template <typename R, int SF, int PIN, int PL, int NR, class Epi>
-__global__ void __launch_bounds__(DSLASH_BS) dslash_kernel(DslashArgs a, Epi epi) {
+__global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_kernel(DslashArgs a, Epi epi) {
   dslash_block<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
 }
 

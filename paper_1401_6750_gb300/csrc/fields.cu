@@ -34,14 +34,18 @@ template <bool BF>
 __global__ void pack_links_16(const double2* __restrict__ src, uint4* __restrict__ dst, int V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
-  uint2* dst2 = reinterpret_cast<uint2*>(dst + 4 * (size_t)V);
   for (int mu = 0; mu < 4; ++mu) {
     const double2* u = src + ((size_t)i * 4 + mu) * 9;
-    uint32_t w[6];
-    for (int k = 0; k < 6; ++k)
+    uint32_t w[9];
+    for (int k = 0; k < 9; ++k)
       w[k] = BF ? f2b((float)u[k].x, (float)u[k].y) : f2h((float)u[k].x, (float)u[k].y);
     dst[(size_t)mu * V + i] = make_uint4(w[0], w[1], w[2], w[3]);
-    dst2[(size_t)mu * V + i] = make_uint2(w[4], w[5]);
+#ifdef TSM_LINK16_FULL
+    dst[4 * (size_t)V + (size_t)mu * V + i] = make_uint4(w[4], w[5], w[6], w[7]);
+    reinterpret_cast<uint32_t*>(dst + 8 * (size_t)V)[(size_t)mu * V + i] = w[8];
+#else
+    reinterpret_cast<uint2*>(dst + 4 * (size_t)V)[(size_t)mu * V + i] = make_uint2(w[4], w[5]);
+#endif
   }
 }
 

@@ -134,8 +134,7 @@ struct Solver {
     a.in = in;
     a.nrhs = nrhs;
     a.nblk = (g->geom.V + DSLASH_BS - 1) / DSLASH_BS;
-    a.kappa = kappa;
-    a.tw = tw;
+    set_coeffs(a, kappa, tw);
     return a;
   }
 
