@@ -32,7 +32,11 @@ def norm2(a):
 
 def cg_normal(u, b, kappa, mu, rho, max_iter, x0=None):
     """Solve (M^dag M) x = b.  Returns (x, iterations, true relative residual)."""
-    apply = lambda v: dirac.apply_MdagM(u, v, kappa, mu)
+    return cg(lambda v: dirac.apply_MdagM(u, v, kappa, mu), b, rho, max_iter, x0)
+
+
+def cg(apply, b, rho, max_iter, x0=None):
+    """The CG above for any Hermitian positive-definite map ``apply``."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     bb = norm2(b)
     if bb == 0.0:
