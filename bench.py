@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--nrhs", type=int, default=32)
     ap.add_argument("--n-hp", type=int, default=2)
     ap.add_argument("--lp", default="f16", choices=["f16", "bf16"])
+    ap.add_argument("--precond", default="eo", choices=["none", "eo"],
+                    help="eo: even-odd (Schur complement) preconditioned CG for both maps")
     ap.add_argument("--dims", default=None, help="Lx,Ly,Lz,T (default 24,24,24,48)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -241,15 +243,16 @@ def probe(args):
             for p in (abi.TSM_F16, abi.TSM_BF16, abi.TSM_F32, abi.TSM_F64):
                 print(json.dumps(_dslash_roofline(g, abi, torch, peak, p, args.nrhs)), flush=True)
     else:
-        lp = abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16
+        flag = abi.TSM_SOLVER_EO if args.precond == "eo" else 0
+        lp = (abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16) | flag
         g.tsm(WORKLOAD["kappa"], WORKLOAD["mu"], args.nrhs, args.n_hp, WORKLOAD["rho_lp"], WORKLOAD["rho_hp"], lp,
-              abi.TSM_SOLVER_F32_RELIABLE, 11, api.momentum_table(9), nrhs_per_launch=args.nrhs)
+              abi.TSM_SOLVER_F32_RELIABLE | flag, 11, api.momentum_table(9), nrhs_per_launch=args.nrhs)
     torch.cuda.synchronize()
     g.close()
     ctx.close()
 
 
-def equal_accuracy(g, abi, torch, w, lp_solver, n_lp=64, n_hp=8, nrhs=32):
+def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs=32):
     """TSM against the plain high-precision path at equal final loop accuracy.
 
     Per-source samples (the scalar and gamma_5 loops of both flavour
@@ -269,7 +272,7 @@ def equal_accuracy(g, abi, torch, w, lp_solver, n_lp=64, n_hp=8, nrhs=32):
 
     def per_source(solver, first, n):
         stream = torch.cuda.current_stream()
-        prec = abi.TSM_F64 if solver in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+        prec = api.solution_prec(solver)
         t = 0.0
         vals = []
         for k0 in range(0, n, nrhs):
@@ -292,7 +295,7 @@ def equal_accuracy(g, abi, torch, w, lp_solver, n_lp=64, n_hp=8, nrhs=32):
         return np.array(vals), t / n
 
     lp_bulk, t_lp = per_source(lp_solver, 0, n_lp)
-    hp, t_hp = per_source(abi.TSM_SOLVER_F32_RELIABLE, n_lp, n_hp)
+    hp, t_hp = per_source(hp_solver, n_lp, n_hp)
     lp_corr, _ = per_source(lp_solver, n_lp, n_hp)
 
     def var(a):  # real and imaginary parts, per observable
@@ -346,7 +349,9 @@ def main():
     ctx = api.Context(local)
     g = api.Gauge(ctx, links, dims, w["t_bc"], precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16, abi.TSM_BF16))
     del links
-    lp_solver = abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16
+    flag = abi.TSM_SOLVER_EO if args.precond == "eo" else 0
+    lp_solver = (abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16) | flag
+    hp_solver = abi.TSM_SOLVER_F32_RELIABLE | flag
     moms = np.ascontiguousarray(np.array(api.momentum_table(w["p2max"]), dtype=np.int32))
     n_mom = moms.shape[0]
     T = dims[3]
@@ -361,7 +366,7 @@ def main():
         # distinct sources every step and on every rank (weak scaling over replicas)
         seed = 1003 + 1000003 * rank + 7919 * step
         return abi.tsm_params(w["kappa"], w["mu"], args.nrhs, args.n_hp, w["rho_lp"], w["rho_hp"], lp_solver,
-                              abi.TSM_SOLVER_F32_RELIABLE, seed, 20000, args.nrhs, n_mom,
+                              hp_solver, seed, 20000, args.nrhs, n_mom,
                               moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
 
     stats_log = []
@@ -456,7 +461,7 @@ def main():
 
     eq = None
     if rank == 0 and not args.no_equal_accuracy:
-        eq = equal_accuracy(g, abi, torch, w, lp_solver)
+        eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -470,6 +475,7 @@ def main():
             "config": {"workload": w["workload"], "dims": dims, "eps": w["eps"], "kappa": w["kappa"], "mu": w["mu"],
                        "lp_solver": "%s storage (links r12, p, Ap), f32 x/r, rho %g" % (args.lp, w["rho_lp"]),
                        "hp_solver": "f32 CG + f64 reliable updates, rho %g" % w["rho_hp"],
+                       "preconditioning": "even-odd (Schur complement on odd sites)" if flag else "none",
                        "sources_per_step": {"lp_bulk": args.nrhs, "hp_correction": args.n_hp},
                        "nrhs_per_launch": args.nrhs, "insertions": 160, "momenta": n_mom,
                        "l2": "inputs larger than L2 (CG working set %.1f GB)" % (

@@ -78,7 +78,14 @@ enum tsm_solver {
   TSM_SOLVER_F64 = 0,          /* FP64 links and vectors throughout             */
   TSM_SOLVER_F32_RELIABLE = 1, /* FP32 CG, FP64 true residual + solution (HP)   */
   TSM_SOLVER_LP_F16 = 2,       /* FP16 links/p/Ap, FP32 x and r (LP)            */
-  TSM_SOLVER_LP_BF16 = 3       /* BF16 links/p/Ap, FP32 x and r (LP)            */
+  TSM_SOLVER_LP_BF16 = 3,      /* BF16 links/p/Ap, FP32 x and r (LP)            */
+  /* Flag OR-ed into any of the above: solve the even-odd (Schur complement)
+   * system Mhat s_o = eta_o - M_oe M_ee^{-1} eta_e by CG on Mhat^dag Mhat on the
+   * odd sites, then reconstruct s_e = M_ee^{-1}(eta_e - M_eo s_o).  Same
+   * solutions and output layout; needs an even L[0].  `rho` then bounds the
+   * residual of the preconditioned normal equations, and the stats report
+   * it.  Not available in tsm_solve_batch. */
+  TSM_SOLVER_EO = 16
 };
 
 #define TSM_N_INSERTIONS 160

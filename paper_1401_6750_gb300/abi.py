@@ -17,6 +17,7 @@ TSM_ERR_NOT_CONVERGED, TSM_ERR_NONFINITE, TSM_ERR_UNIMPLEMENTED = 4, 5, 6
 TSM_F64, TSM_F32, TSM_F16, TSM_BF16 = 0, 1, 2, 3
 TSM_OP_M, TSM_OP_MDAG, TSM_OP_A, TSM_OP_MDAGM = 0, 1, 2, 3
 TSM_SOLVER_F64, TSM_SOLVER_F32_RELIABLE, TSM_SOLVER_LP_F16, TSM_SOLVER_LP_BF16 = 0, 1, 2, 3
+TSM_SOLVER_EO = 16  # flag: even-odd preconditioned CG (OR with a solver)
 TSM_N_INSERTIONS = 160
 TSM_CONTRACT_NOALLOC_MAX_BYTES = 32 * 1024 * 1024
 CHUNKS = {TSM_F64: 12, TSM_F32: 6, TSM_F16: 3, TSM_BF16: 3}

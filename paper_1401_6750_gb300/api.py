@@ -20,7 +20,8 @@ def _stream(stream=None):
 
 def solution_prec(solver):
     """Native precision of the solutions a solver returns."""
-    return abi.TSM_F64 if solver in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+    kind = solver & ~abi.TSM_SOLVER_EO
+    return abi.TSM_F64 if kind in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
 
 
 def _ptr(t):

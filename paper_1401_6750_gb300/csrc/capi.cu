@@ -237,7 +237,8 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src, int 
 
 static int check_solver_args(const tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter) {
   if (!g) return fail(TSM_ERR_INVALID_ARG, "gauge is NULL");
-  if (solver < TSM_SOLVER_F64 || solver > TSM_SOLVER_LP_BF16) return fail(TSM_ERR_INVALID_ARG, "bad solver %d", solver);
+  if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver %d", solver);
+  if ((solver & TSM_SOLVER_EO) && g->geom.L[0] % 2) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need an even L[0]");
   if (!(rho > 0.0) || !(rho < 1.0)) return fail(TSM_ERR_INVALID_ARG, "rho must lie in (0, 1), got %g", rho);
   if (max_iter < 1) return fail(TSM_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (!isfinite(kappa) || !isfinite(mu) || kappa <= 0.0) return fail(TSM_ERR_INVALID_ARG, "bad kappa or mu");
@@ -276,6 +277,7 @@ int tsm_solve_sources(tsm_gauge* g, double kappa, double mu, int solver, double 
 
 int tsm_solve_batch(tsm_batch_item* items, int n_items, int solver, double rho, int max_iter, void* stream) {
   if (!items || n_items < 1 || n_items > 64) return fail(TSM_ERR_INVALID_ARG, "need 1 to 64 batch items");
+  if (solver & TSM_SOLVER_EO) return fail(TSM_ERR_INVALID_ARG, "tsm_solve_batch has no even-odd variant");
   long long rhs = 0;
   for (int k = 0; k < n_items; ++k) {
     const tsm_batch_item& it = items[k];
@@ -343,7 +345,7 @@ int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec, const vo
   if (!g || !s_dev || !grad_dev || !dmu_host || nsrc < 1 || n_mom < 1 || !mom)
     return fail(TSM_ERR_INVALID_ARG, "tsm_loops_backward: bad argument");
   if (prec != TSM_F64 && prec != TSM_F32) return fail(TSM_ERR_INVALID_ARG, "solutions must be F64 or F32");
-  if (solver != TSM_SOLVER_F64 && solver != TSM_SOLVER_F32_RELIABLE)
+  if (solver_kind(solver) != TSM_SOLVER_F64 && solver_kind(solver) != TSM_SOLVER_F32_RELIABLE)
     return fail(TSM_ERR_INVALID_ARG, "the adjoint solve needs TSM_SOLVER_F64 or TSM_SOLVER_F32_RELIABLE");
   TSM_TRY(check_solver_args(g, kappa, mu, solver, rho, max_iter));
   if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);

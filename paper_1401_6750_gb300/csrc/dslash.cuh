@@ -43,6 +43,48 @@ struct DslashArgs {
   double kappa;
   double tw;          // twist coefficient multiplying i g5
   float kappa_f, tw_f;  // the same, pre-rounded for FP32 kernels (no per-thread FP64 conversion)
+  // checkerboarded operator (even-odd kernels only):
+  //   out(j) = (c0 + i c1 g5) center(j) + (h0 + i h1 g5) hop(in)(j)
+  // on the sites of parity `parity`, j = full site >> 1; center may be null.
+  const void* center;
+  int parity;
+  double c0, c1, h0, h1;
+  float c0_f, c1_f, h0_f, h1_f;
+};
+
+__host__ __device__ inline void set_eo(DslashArgs& a, const void* center, int parity, double c0, double c1, double h0,
+                                       double h1) {
+  a.center = center;
+  a.parity = parity;
+  a.c0 = c0;
+  a.c1 = c1;
+  a.h0 = h0;
+  a.h1 = h1;
+  a.c0_f = (float)c0;
+  a.c1_f = (float)c1;
+  a.h0_f = (float)h0;
+  a.h1_f = (float)h1;
+}
+
+template <typename R>
+struct EoCoef;
+template <>
+struct EoCoef<float> {
+  __device__ static void get(const DslashArgs& a, float& c0, float& c1, float& h0, float& h1) {
+    c0 = a.c0_f;
+    c1 = a.c1_f;
+    h0 = a.h0_f;
+    h1 = a.h1_f;
+  }
+};
+template <>
+struct EoCoef<double> {
+  __device__ static void get(const DslashArgs& a, double& c0, double& c1, double& h0, double& h1) {
+    c0 = a.c0;
+    c1 = a.c1;
+    h0 = a.h0;
+    h1 = a.h1;
+  }
 };
 
 template <typename R>
@@ -215,10 +257,13 @@ __device__ __forceinline__ void hop_accumulate(cplx<R> (&acc)[12], const cplx<R>
 
 // Both hops of direction MU for NR right-hand sides r0 .. r0+NR-1 (slots with
 // act[j] false are skipped); each link is loaded and rebuilt once.
-template <int MU, int SF, typename R, int PIN, int PL, int NR>
+// Checkerboarded fields (EO = true) hold one parity at index i >> 1 with
+// stride V / 2; links are always indexed by the full site.
+template <int MU, int SF, typename R, int PIN, int PL, int NR, bool EO = false>
 __device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[NR][12], const DslashArgs& a, int r0,
                                             const bool (&act)[NR], int i, const int c[4]) {
   const size_t V = (size_t)a.g.V;
+  const size_t FS = EO ? V / 2 : V;
   const int stride = dir_stride(a.g, MU);
   cplx<R> u[3][3];
   cplx<R> h0[3], h1[3];
@@ -229,7 +274,7 @@ __device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[NR][12], const Dslash
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       if (!act[j]) continue;
-      ProjLoad<MU, SF, PIN, R>::run(h0, h1, a.in, V, r0 + j, n);
+      ProjLoad<MU, SF, PIN, R>::run(h0, h1, a.in, FS, r0 + j, EO ? (n >> 1) : n);
       hop_accumulate<MU, SF, false>(acc[j], h0, h1, u, sgn);
     }
   }
@@ -240,7 +285,7 @@ __device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[NR][12], const Dslash
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       if (!act[j]) continue;
-      ProjLoad<MU, -SF, PIN, R>::run(h0, h1, a.in, V, r0 + j, n);
+      ProjLoad<MU, -SF, PIN, R>::run(h0, h1, a.in, FS, r0 + j, EO ? (n >> 1) : n);
       hop_accumulate<MU, -SF, true>(acc[j], h0, h1, u, sgn);
     }
   }
@@ -347,6 +392,97 @@ __device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi
 template <typename R, int SF, int PIN, int PL, int NR, class Epi>
 __global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_kernel(DslashArgs a, Epi epi) {
   dslash_block<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
+}
+
+// ---------------------------------------------------------------- even-odd operator
+// Full site of checkerboard index j on parity p (Lx even: sites 2j and 2j+1
+// share y, z, t and have opposite parity).
+__device__ __forceinline__ int eo_site(const Geom& g, int j, int p, int c[4]) {
+  const int i0 = 2 * j;
+  site_coords(g, i0, c);
+  const int b = (p - (c[1] + c[2] + c[3])) & 1;  // x of i0 is even
+  c[0] += b;
+  return i0 + b;
+}
+
+template <int SF, typename R, int PIN, int PL, int NR>
+__device__ __forceinline__ void apply_site_eo(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0,
+                                              const bool (&act)[NR], int j) {
+  int c[4];
+  const int i = eo_site(a.g, j, a.parity, c);
+#pragma unroll
+  for (int q = 0; q < NR; ++q)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[q][k] = mk<R>(0, 0);
+  stencil_dir<0, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  stencil_dir<1, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  stencil_dir<2, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  stencil_dir<3, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  R c0, c1, h0, h1;
+  EoCoef<R>::get(a, c0, c1, h0, h1);
+  const size_t FS = (size_t)a.g.V / 2;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    if (!act[q]) continue;
+    cplx<R> ctr[12];
+    if (a.center) {
+      SpinorIO<PIN>::load(a.center, FS, r0 + q, j, ctr);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) ctr[k] = mk<R>(0, 0);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const R g5 = (k < 6) ? (R)1 : (R)-1;
+      const cplx<R> hv = out[q][k];
+      out[q][k] = c0 * ctr[k] + (g5 * c1) * times_i(ctr[k]) + h0 * hv + (g5 * h1) * times_i(hv);
+    }
+  }
+}
+
+template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+__device__ __forceinline__ void dslash_block_eo(const DslashArgs& a, const Epi& epi, int bid) {
+  __shared__ double sh[32];
+  const int ngrp = (a.nrhs + NR - 1) / NR;
+  const int grp = bid % ngrp;
+  const int blk = bid / ngrp;
+  const int r0 = grp * NR;
+  bool act[NR];
+  bool any = false;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    act[q] = (r0 + q < a.nrhs) && epi.active(r0 + q);
+    any |= act[q];
+  }
+  if (!any) return;
+  const int j = blk * DSLASH_BS + threadIdx.x;
+  R red[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) red[q] = (R)0;
+  if (j < a.g.V / 2) {
+    cplx<R> out[NR][12];
+    apply_site_eo<SF, R, PIN, PL, NR>(out, a, r0, act, j);
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (act[q]) red[q] = epi.site(r0 + q, j, out[q]);
+  }
+  if (Epi::kReduce) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q)
+      if (act[q]) reduce_and_finalize(epi, epi.red, r0 + q, a.nblk, blk, (double)red[q], sh);
+  }
+}
+
+template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+__global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_eo_kernel(DslashArgs a, Epi epi) {
+  dslash_block_eo<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
+}
+
+// a.nblk must be ceil(V/2 / DSLASH_BS).  One right-hand side per thread.
+template <typename R, int SF, int PIN, int PL, class Epi>
+inline void launch_dslash_eo(const DslashArgs& a, const Epi& e, cudaStream_t s) {
+  const unsigned grid = (unsigned)a.nblk * (unsigned)a.nrhs;
+  dslash_eo_kernel<R, SF, PIN, PL, 1, Epi><<<grid, DSLASH_BS, 0, s>>>(a, e);
 }
 
 // Plain store of the result (optionally times g5), no reduction.

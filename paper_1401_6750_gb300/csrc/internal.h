@@ -80,6 +80,10 @@ struct GradWorkspace;  // grad.cu
 struct GradWsDeleter {
   void operator()(GradWorkspace* w) const;  // grad.cu
 };
+struct EoWorkspace;  // eo.cu
+struct EoWsDeleter {
+  void operator()(EoWorkspace* w) const;  // eo.cu
+};
 
 }  // namespace tsm
 
@@ -96,6 +100,7 @@ struct tsm_gauge {
   tsm::DevBuf links[4];
   std::mutex mu;  // guards the caches below
   std::map<long long, std::unique_ptr<tsm::SolverWorkspace, tsm::SolverWsDeleter>> solver_ws;
+  std::map<long long, std::unique_ptr<tsm::EoWorkspace, tsm::EoWsDeleter>> eo_ws;
   std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws;
   tsm::DevBuf tmp;  // operator scratch (M^dag M intermediate, conversions)
   std::mutex tsm_mu;       // guards the TSM buffers
@@ -148,6 +153,15 @@ int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double r
                      const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
                      int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
 int solver_precise_prec(int solver);
+// The same with the even-odd preconditioned CG (solver carries TSM_SOLVER_EO; eo.cu).
+int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
+                   const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
+                   int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
+// solver kind without flags; -1 if unknown
+inline int solver_kind(int solver) {
+  const int k = solver & ~TSM_SOLVER_EO;
+  return (k >= TSM_SOLVER_F64 && k <= TSM_SOLVER_LP_BF16) ? k : -1;
+}
 int solve_batch_multi(tsm_batch_item* items, int n, int solver, double rho, int max_iter, cudaStream_t s);
 int solver_output_prec(int solver);
 unsigned solver_link_precs(int solver);

@@ -60,13 +60,15 @@ struct SolverWorkspace {
 void SolverWsDeleter::operator()(SolverWorkspace* w) const { delete w; }
 
 int solver_precise_prec(int solver) {
+  solver &= ~TSM_SOLVER_EO;
   return (solver == TSM_SOLVER_F64 || solver == TSM_SOLVER_F32_RELIABLE) ? TSM_F64 : TSM_F32;
 }
 int solver_output_prec(int solver) {
+  solver &= ~TSM_SOLVER_EO;
   return (solver == TSM_SOLVER_F64 || solver == TSM_SOLVER_F32_RELIABLE) ? TSM_F64 : TSM_F32;
 }
 unsigned solver_link_precs(int solver) {
-  switch (solver) {
+  switch (solver & ~TSM_SOLVER_EO) {
     case TSM_SOLVER_F64: return TSM_PREC_BIT(TSM_F64);
     case TSM_SOLVER_F32_RELIABLE: return TSM_PREC_BIT(TSM_F32) | TSM_PREC_BIT(TSM_F64);
     case TSM_SOLVER_LP_F16: return TSM_PREC_BIT(TSM_F16) | TSM_PREC_BIT(TSM_F32);
@@ -384,6 +386,9 @@ int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double r
   if ((g->precisions & need) != need)
     return fail(TSM_ERR_INVALID_ARG, "solver %d needs gauge copies 0x%x, gauge has 0x%x", solver, need,
                 g->precisions);
+  if (solver & TSM_SOLVER_EO)
+    return solve_batch_eo(g, kappa, mu, solver, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec, x_out,
+                          gamma5_io, stats, s);
   switch (solver) {
     case TSM_SOLVER_F64:
       return solve_kind<TSM_SOLVER_F64>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec,

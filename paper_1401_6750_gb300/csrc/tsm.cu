@@ -50,7 +50,7 @@ struct Accum {
 int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho, uint64_t first, int n,
                        int batch, DevBuf& sol, double* acc, Accum& a, cudaStream_t s) {
   // loops are contracted in FP64 for the all-FP64 solver and in FP32 otherwise
-  const int op = (solver == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
+  const int op = (solver_kind(solver) == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
   std::vector<tsm_solve_stats> st(batch);
   for (int k0 = 0; k0 < n; k0 += batch) {
     const int nb = std::min(batch, n - k0);
@@ -80,7 +80,8 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
   if (p->n_lp < 1 || p->n_hp < 0) return fail(TSM_ERR_INVALID_ARG, "need n_lp >= 1 and n_hp >= 0");
   if (p->n_mom < 1 || !p->mom) return fail(TSM_ERR_INVALID_ARG, "need at least one momentum");
   for (int solver : {p->lp_solver, p->hp_solver}) {
-    if (solver < TSM_SOLVER_F64 || solver > TSM_SOLVER_LP_BF16) return fail(TSM_ERR_INVALID_ARG, "bad solver");
+    if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver");
+    if ((solver & TSM_SOLVER_EO) && g->geom.L[0] % 2) return fail(TSM_ERR_INVALID_ARG, "even-odd needs an even L[0]");
     const unsigned need = solver_link_precs(solver);
     if ((g->precisions & need) != need)
       return fail(TSM_ERR_INVALID_ARG, "solver %d needs gauge copies 0x%x", solver, need);

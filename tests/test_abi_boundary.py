@@ -50,3 +50,15 @@ def test_invalid_arguments_rejected_before_device_use(lib):
     assert lib.tsm_solve_tsm(None, None, None, None, None, None) == abi.TSM_ERR_INVALID_ARG
     assert b"NULL" in lib.tsm_last_error() or len(lib.tsm_last_error()) > 0
     assert lib.tsm_spinor_bytes(None, 0, 1) == 0
+
+
+def test_header_enum_values_match_binding():
+    """Every TSM_* enumerator of the header has the value the binding uses."""
+    import os
+    import re
+    text = open(os.path.join(build.INCLUDE, "tsm.h")).read()
+    found = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(TSM_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    assert "TSM_SOLVER_EO" in found and "TSM_SOLVER_LP_BF16" in found
+    for name, value in found.items():
+        if hasattr(abi, name):
+            assert getattr(abi, name) == value, name
