@@ -272,7 +272,8 @@ def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs
 
     def per_source(solver, first, n):
         stream = torch.cuda.current_stream()
-        prec = api.solution_prec(solver)
+        kind = solver & ~abi.TSM_SOLVER_EO
+        prec = abi.TSM_F64 if kind in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
         t = 0.0
         vals = []
         for k0 in range(0, n, nrhs):

@@ -76,7 +76,9 @@ enum tsm_op {
 /* Solvers for Eq. 1 (all CG on M^dag M, x0 = 0, see tsm_solve_sources). */
 enum tsm_solver {
   TSM_SOLVER_F64 = 0,          /* FP64 links and vectors throughout             */
-  TSM_SOLVER_F32_RELIABLE = 1, /* FP32 CG, FP64 true residual + solution (HP)   */
+  TSM_SOLVER_F32_RELIABLE = 1, /* FP32 CG; true residual and solution sum in     *
+                                * float-float (about 44 significant bits), for  *
+                                * rho down to about 1e-10 (HP); tighter: F64    */
   TSM_SOLVER_LP_F16 = 2,       /* FP16 links/p/Ap, FP32 x and r (LP)            */
   TSM_SOLVER_LP_BF16 = 3,      /* BF16 links/p/Ap, FP32 x and r (LP)            */
   /* Flag OR-ed into any of the above: solve the even-odd (Schur complement)

@@ -37,7 +37,7 @@ struct InstDesc {
   int eblk;     // element-wise blocks per right-hand side
   int eblock0;  // first element-wise block
   void *b, *t, *x, *r, *p, *q;
-  double2* xacc;
+  void* xacc;
   RhsState* st;
   double* partial;
   unsigned* counter;
@@ -132,7 +132,7 @@ __global__ void multi_init(const InstDesc* __restrict__ d, int n) {
   for (int k = 0; k < 12; ++k) z[k] = mk<double>(0.0, 0.0);
   SpinorIO<T::PA>::store(I.r, V, rhs, i, v);
   SpinorIO<T::PA>::store(I.x, V, rhs, i, z);
-  if (T::XACC) SpinorIO<TSM_F64>::store(I.xacc, V, rhs, i, z);
+  if (T::XACC) SpinorIO<T::PXA>::store(I.xacc, V, rhs, i, z);
   const double c = I.st[rhs].c_r;
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = c * v[k];
@@ -166,13 +166,13 @@ __global__ void multi_fold(const InstDesc* __restrict__ d, int n) {
   const size_t V = (size_t)I.g.V;
   cplx<double> xv[12], av[12];
   SpinorIO<T::PA>::load(I.x, V, rhs, i, xv);
-  SpinorIO<TSM_F64>::load(I.xacc, V, rhs, i, av);
+  SpinorIO<T::PXA>::load(I.xacc, V, rhs, i, av);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     av[k] = av[k] + xv[k];
     xv[k] = mk<double>(0.0, 0.0);
   }
-  SpinorIO<TSM_F64>::store(I.xacc, V, rhs, i, av);
+  SpinorIO<T::PXA>::store(I.xacc, V, rhs, i, av);
   SpinorIO<T::PA>::store(I.x, V, rhs, i, xv);
 }
 
@@ -186,7 +186,7 @@ __global__ void multi_output(const InstDesc* __restrict__ d, int n) {  // t = x 
   SpinorIO<T::PA>::load(I.x, V, rhs, i, v);
   if (T::XACC) {
     cplx<double> a[12];
-    SpinorIO<TSM_F64>::load(I.xacc, V, rhs, i, a);
+    SpinorIO<T::PXA>::load(I.xacc, V, rhs, i, a);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = v[k] + a[k];
   }
@@ -226,7 +226,7 @@ struct Multi {
       TSM_TRY(B.r.reserve(fbytes(T::PA, V, m)));
       TSM_TRY(B.p.reserve(fbytes(T::PS, V, m)));
       TSM_TRY(B.q.reserve(fbytes(T::PS, V, m)));
-      if (T::XACC) TSM_TRY(B.xacc.reserve(fbytes(TSM_F64, V, m)));
+      if (T::XACC) TSM_TRY(B.xacc.reserve(fbytes(T::PXA, V, m)));
       const int nblk = (V + DSLASH_BS - 1) / DSLASH_BS;
       TSM_TRY(B.st.reserve(sizeof(RhsState) * m));
       TSM_TRY(B.partial.reserve(sizeof(double) * (size_t)nblk * m));
@@ -251,7 +251,7 @@ struct Multi {
       I.r = B.r.p;
       I.p = B.p.p;
       I.q = B.q.p;
-      I.xacc = B.xacc.as<double2>();
+      I.xacc = B.xacc.p;
       I.st = B.st.as<RhsState>();
       I.partial = B.partial.as<double>();
       I.counter = B.counter.as<unsigned>();

@@ -13,6 +13,61 @@
 
 namespace tsm {
 
+// Internal storage precision of the precise operator of the reliable-update
+// solver: each real as a pair of floats (hi + lo), 16 bytes per complex like
+// TSM_F64.  Not part of the public precision enumeration.
+constexpr int TSM_DS = 4;
+
+// ---------------------------------------------------------------- float-float
+// A real carried as an unevaluated sum hi + lo of two floats (about 44 bits
+// of significand after a few dozen operations), so that the FP32 pipes do the
+// work of an FP64 operator.  Sums use Knuth's TwoSum (TAOCP vol. 2, 4.2.2)
+// for the leading parts and add the trailing parts with plain float adds;
+// products use the FMA form of Dekker's exact product (Dekker 1971) plus the
+// cross and lo * lo terms.  lo is left unnormalised between operations and
+// renormalised (TwoSum) when stored.
+struct dsf {
+  float hi, lo;
+  dsf() = default;
+  __host__ __device__ __forceinline__ dsf(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ dsf(float v) : hi(v), lo(0.0f) {}
+  __host__ __device__ __forceinline__ dsf(int v) : hi((float)v), lo(0.0f) {}
+  __host__ __device__ __forceinline__ dsf(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ dsf operator+(dsf a, dsf b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);
+  return dsf(s, e + (a.lo + b.lo));
+}
+__device__ __forceinline__ dsf operator-(dsf a) { return dsf(-a.hi, -a.lo); }
+__device__ __forceinline__ dsf& operator+=(dsf& a, dsf b) { return a = a + b; }
+__device__ __forceinline__ dsf operator-(dsf a, dsf b) { return a + (-b); }
+// The lo * lo term stays: after a cancellation lo can exceed hi, and the
+// square of such a value (a residual component) needs it.
+__device__ __forceinline__ dsf operator*(dsf a, dsf b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  e = fmaf(a.lo, b.lo, e);
+  return dsf(p, e);
+}
+// a * b + c for every real type of the kernels (exact-type overloads)
+__device__ __forceinline__ float fmar(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmar(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ dsf fmar(dsf a, dsf b, dsf c) { return a * b + c; }
+// hi = fl(hi + lo), lo = the rounding error (TwoSum: exact whatever the
+// relative size of the parts)
+__device__ __forceinline__ dsf normalise(dsf a) {
+  const float s = a.hi + a.lo;
+  const float bb = s - a.hi;
+  return dsf(s, (a.hi - (s - bb)) + (a.lo - bb));
+}
+
 // ---------------------------------------------------------------- complex
 template <typename R>
 struct cplx {
@@ -44,18 +99,18 @@ __device__ __forceinline__ cplx<R> cmulc(cplx<R> a, cplx<R> b) {
 // acc += a * b
 template <typename R>
 __device__ __forceinline__ void cmac(cplx<R>& acc, cplx<R> a, cplx<R> b) {
-  acc.re = fma(a.re, b.re, acc.re);
-  acc.re = fma(-a.im, b.im, acc.re);
-  acc.im = fma(a.re, b.im, acc.im);
-  acc.im = fma(a.im, b.re, acc.im);
+  acc.re = fmar(a.re, b.re, acc.re);
+  acc.re = fmar(-a.im, b.im, acc.re);
+  acc.im = fmar(a.re, b.im, acc.im);
+  acc.im = fmar(a.im, b.re, acc.im);
 }
 // acc += conj(a) * b
 template <typename R>
 __device__ __forceinline__ void cmacc(cplx<R>& acc, cplx<R> a, cplx<R> b) {
-  acc.re = fma(a.re, b.re, acc.re);
-  acc.re = fma(a.im, b.im, acc.re);
-  acc.im = fma(a.re, b.im, acc.im);
-  acc.im = fma(-a.im, b.re, acc.im);
+  acc.re = fmar(a.re, b.re, acc.re);
+  acc.re = fmar(a.im, b.im, acc.re);
+  acc.im = fmar(a.re, b.im, acc.im);
+  acc.im = fmar(-a.im, b.re, acc.im);
 }
 template <typename R>
 __device__ __forceinline__ cplx<R> times_i(cplx<R> a) { return mk(-a.im, a.re); }
@@ -223,7 +278,48 @@ struct SpinorIO<TSM_F16> : Half16IO<false> {};
 template <>
 struct SpinorIO<TSM_BF16> : Half16IO<true> {};
 
-__host__ __device__ constexpr int spinor_chunks(int p) { return p == TSM_F64 ? 12 : (p == TSM_F32 ? 6 : 3); }
+// float-float: one float4 (re.hi, re.lo, im.hi, im.lo) per complex, 12 chunks
+template <typename R>
+__device__ __forceinline__ R from_pair(float h, float l) {
+  return (R)((double)h + (double)l);
+}
+template <>
+__device__ __forceinline__ float from_pair<float>(float h, float l) { return h + l; }
+template <>
+__device__ __forceinline__ dsf from_pair<dsf>(float h, float l) { return dsf(h, l); }
+template <typename R>
+__device__ __forceinline__ dsf to_pair(R v) { return dsf((double)v); }
+template <>
+__device__ __forceinline__ dsf to_pair<float>(float v) { return dsf(v); }
+template <>
+__device__ __forceinline__ dsf to_pair<dsf>(dsf v) { return normalise(v); }
+
+template <>
+struct SpinorIO<TSM_DS> {
+  static constexpr int NCH = 12;
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int r, int i, cplx<R> (&v)[12]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float4 d = __ldg(p + k * V);
+      v[k] = mk<R>(from_pair<R>(d.x, d.y), from_pair<R>(d.z, d.w));
+    }
+  }
+  template <typename R>
+  __device__ __forceinline__ static void store(void* base, size_t V, int r, int i, const cplx<R> (&v)[12]) {
+    float4* p = reinterpret_cast<float4*>(base) + (size_t)r * NCH * V + i;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const dsf a = to_pair<R>(v[k].re), b = to_pair<R>(v[k].im);
+      p[k * V] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+  }
+};
+
+__host__ __device__ constexpr int spinor_chunks(int p) {
+  return (p == TSM_F64 || p == TSM_DS) ? 12 : (p == TSM_F32 ? 6 : 3);
+}
 
 // ---------------------------------------------------------------- links
 // F64: [4][9][V] double2, all entries U_ab (k = 3a + b).
@@ -312,10 +408,25 @@ struct LinkIO<TSM_F16> : Link16IO<false> {};
 template <>
 struct LinkIO<TSM_BF16> : Link16IO<true> {};
 
+// float-float links: [4][9][V] float4 (re.hi, re.lo, im.hi, im.lo), all entries
+template <>
+struct LinkIO<TSM_DS> {
+  template <typename R>
+  __device__ __forceinline__ static void load(const void* base, size_t V, int mu, int i, cplx<R> (&u)[3][3]) {
+    const float4* p = reinterpret_cast<const float4*>(base) + (size_t)mu * 9 * V + i;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 d = __ldg(p + k * V);
+      u[k / 3][k % 3] = mk<R>(from_pair<R>(d.x, d.y), from_pair<R>(d.z, d.w));
+    }
+  }
+};
+
 // bytes of one device gauge copy of precision p
 inline size_t link_bytes(int p, size_t V) {
   switch (p) {
-    case TSM_F64: return 4 * 9 * V * 16;
+    case TSM_F64:
+    case TSM_DS: return 4 * 9 * V * 16;
     case TSM_F32: return 4 * 3 * V * 16;
 #ifdef TSM_LINK16_FULL
     default: return 4 * V * 16 * 2 + 4 * V * 4;

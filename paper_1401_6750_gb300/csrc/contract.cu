@@ -106,104 +106,114 @@ int build_gamma_table(GammaTable& t) {
 }
 
 constexpr int NF = 32;       // fields per pass: 2 flavour structures x 16
-constexpr int K4_BS = 256;
+constexpr int FLD_BS = 128;  // site-field kernel block
+constexpr int XY_BS = 256;   // x/y transform block
+constexpr int XY_NC = 7;     // momenta per accumulator set
 constexpr int Z_BS = 256;
 
+// Site fields (summed over the sources) in F[(pass*NF + f) * V + i], site fastest.
 template <typename R>
-struct ContractArgs {
+struct FieldArgs {
   Geom g;
   const void* s;
   const void* v;
   const void* links;
   int nsrc;
-  int rad;  // max |n_i|
-  int nx;   // 2 rad + 1
-  int rb;   // rows per row block
-  double2* part;  // [Lz*T][nx*nx][160]
+  cplx<R>* F;
 };
 
 template <typename R>
-__device__ __forceinline__ void matvec(cplx<R> (&w)[12], const cplx<R> (&u)[3][3], const cplx<R> (&p)[12],
-                                       bool dag, R sgn) {
+__device__ __forceinline__ void matvec(cplx<R> (&w)[12], const cplx<R> (&u)[3][3], const cplx<R> (&p)[12], R sgn) {
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       cplx<R> t = mk<R>(0, 0);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        if (dag)
-          cmacc(t, u[b][a], p[3 * sp + b]);
-        else
-          cmac(t, u[a][b], p[3 * sp + b]);
-      }
+      for (int b = 0; b < 3; ++b) cmac(t, u[a][b], p[3 * sp + b]);
       w[3 * sp + a] = sgn * t;
     }
 }
 
-// acc[a*4+b] += g_a * scale * sum_c conj(l_ac) r_bc
-template <typename R>
-__device__ __forceinline__ void outer(cplx<R>* acc, const cplx<R> (&l)[12], const cplx<R> (&r)[12], R scale) {
+// acc[a*4+b] += sum_c conj(l_ac) r_bc   (times -1 when SUB)
+template <bool SUB, typename R>
+__device__ __forceinline__ void outer(cplx<R> (&acc)[16], const cplx<R> (&l)[12], const cplx<R> (&r)[12]) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const R ga = (a < 2 ? scale : -scale);
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      cplx<R> t = mk<R>(0, 0);
+    for (int b = 0; b < 4; ++b)
 #pragma unroll
-      for (int c = 0; c < 3; ++c) cmacc(t, l[3 * a + c], r[3 * b + c]);
-      acc[4 * a + b] = acc[4 * a + b] + ga * t;
-    }
-  }
+      for (int c = 0; c < 3; ++c) {
+        if (SUB)
+          cmacc(acc[4 * a + b], mk<R>(-l[3 * a + c].re, -l[3 * a + c].im), r[3 * b + c]);
+        else
+          cmacc(acc[4 * a + b], l[3 * a + c], r[3 * b + c]);
+      }
 }
 
-// Fields of pass P at site i, summed over the sources: 32 complex.
+// The symmetric covariant derivative at x collapses onto forward products:
+//   O_mu(x) = 1/4 [D_mu(x) + D_mu(x - mu)],
+//   D^0_mu(y)[a][b] = g_a (M[a][b] - conj(M[b][a])),  M = sum_c conj(s_ac(y)) (U_mu(y) s(y+mu))_bc
+//   D^1_mu(y)[a][b] = g_a sum_c [conj(s_ac(y)) (U_mu(y) v(y+mu))_bc - conj((U_mu(y) s(y+mu))_ac) v_bc(y)]
+// (the two backward terms of O at x are the forward products rooted at
+// x - mu).  The shift is applied after the projection: a phase
+// (1 + e^{-i p_mu}) for spatial mu, the sum of timeslices t and t-1 for mu = t.
+// Pass 0 holds the ultra-local D^0 = g_a sum_c conj(s_ac) s_bc and D^1 with v.
 template <typename R, int PS, int PL>
-__device__ void site_fields(cplx<R> (&acc)[NF], const ContractArgs<R>& a, int pass, int i, const int c[4]) {
-#pragma unroll
-  for (int f = 0; f < NF; ++f) acc[f] = mk<R>(0, 0);
+__global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) contract_fields_kernel(FieldArgs<R> a) {
+  const int pass = blockIdx.x % 5;
+  const int i = (blockIdx.x / 5) * FLD_BS + threadIdx.x;
+  if (i >= a.g.V) return;
   const size_t V = (size_t)a.g.V;
+  cplx<R> m0[16], m1[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) m0[k] = m1[k] = mk<R>(0, 0);
+  R scale = (R)1;
   if (pass == 0) {
     for (int r = 0; r < a.nsrc; ++r) {
       cplx<R> s0[12], v0[12];
       SpinorIO<PS>::load(a.s, V, r, i, s0);
       SpinorIO<PS>::load(a.v, V, r, i, v0);
-      outer(acc, s0, s0, (R)1);
-      outer(acc + 16, s0, v0, (R)1);
+      outer<false>(m0, s0, s0);
+      outer<false>(m1, s0, v0);
     }
-    return;
+  } else {
+    const int mu = pass - 1;
+    int c[4];
+    site_coords(a.g, i, c);
+    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    cplx<R> u[3][3];
+    LinkIO<PL>::load(a.links, V, mu, i, u);
+    const R sf = (mu == 3 && c[3] == a.g.L[3] - 1) ? (R)a.g.bc : (R)1;
+    for (int r = 0; r < a.nsrc; ++r) {
+      cplx<R> t[12], w[12], s0[12];
+      SpinorIO<PS>::load(a.s, V, r, nf, t);
+      matvec(w, u, t, sf);                   // U s(y+mu)
+      SpinorIO<PS>::load(a.s, V, r, i, s0);
+      outer<false>(m0, s0, w);
+      SpinorIO<PS>::load(a.v, V, r, i, t);
+      outer<true>(m1, w, t);                 // - conj(U s(y+mu)) v(y)
+      SpinorIO<PS>::load(a.v, V, r, nf, t);
+      matvec(w, u, t, sf);                   // U v(y+mu)
+      outer<false>(m1, s0, w);
+    }
+    // D^0 = M - M^dag (before the g_a row factor)
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = p; q < 4; ++q) {
+        const cplx<R> x = m0[4 * p + q], y = m0[4 * q + p];
+        m0[4 * p + q] = mk<R>(x.re - y.re, x.im + y.im);
+        m0[4 * q + p] = mk<R>(y.re - x.re, y.im + x.im);
+      }
+    scale = (R)0.25;
   }
-  const int mu = pass - 1;
-  const int stride = dir_stride(a.g, mu);
-  const int nf = fwd_site(a.g, i, c, mu, stride);
-  const int nb = bwd_site(a.g, i, c, mu, stride);
-  cplx<R> uf[3][3], ub[3][3];
-  LinkIO<PL>::load(a.links, V, mu, i, uf);
-  LinkIO<PL>::load(a.links, V, mu, nb, ub);
-  const R sf = (mu == 3 && c[3] == a.g.L[3] - 1) ? (R)a.g.bc : (R)1;
-  const R sb = (mu == 3 && c[3] == 0) ? (R)a.g.bc : (R)1;
-  const R q = (R)0.25;
-  for (int r = 0; r < a.nsrc; ++r) {
-    cplx<R> t[12], w0[12], w1[12], s0[12];
-    SpinorIO<PS>::load(a.s, V, r, nf, t);
-    matvec(w0, uf, t, false, sf);
-    SpinorIO<PS>::load(a.s, V, r, nb, t);
-    matvec(w1, ub, t, true, sb);
+  cplx<R>* out = a.F + (size_t)pass * NF * V + i;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) w0[k] = w0[k] - w1[k];  // W^0
-    SpinorIO<PS>::load(a.v, V, r, nf, t);
-    matvec(w1, uf, t, false, sf);
-    cplx<R> tb[12];
-    SpinorIO<PS>::load(a.v, V, r, nb, t);
-    matvec(tb, ub, t, true, sb);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) w1[k] = w1[k] - tb[k];  // W^1
-    SpinorIO<PS>::load(a.s, V, r, i, s0);
-    outer(acc, s0, w0, q);
-    outer(acc, w0, s0, -q);
-    outer(acc + 16, s0, w1, q);
-    SpinorIO<PS>::load(a.v, V, r, i, t);
-    outer(acc + 16, w0, t, -q);
+  for (int k = 0; k < 16; ++k) {
+    const R ga = (k < 8) ? scale : -scale;  // row a = k / 4: g5 = +1 for a < 2
+    out[(size_t)k * V] = ga * m0[k];
+    out[(size_t)(16 + k) * V] = ga * m1[k];
   }
 }
 
@@ -218,82 +228,93 @@ __device__ __forceinline__ void twiddle(cplx<double>& o, int m, int L) {
   o = mk<double>(cs, -sn);
 }
 
-// One block per (z, t) plane: fields -> x transform -> y transform -> part.
-// Shared layouts keep the field index f fastest so that a warp touches
-// consecutive words; F rows are padded by one element against bank conflicts.
-constexpr int FSTR = NF + 1;
-
-template <typename R, int PS, int PL>
-__global__ void __launch_bounds__(K4_BS) contract_plane_kernel(ContractArgs<R> a) {
+// x then y transform of the 160 site fields of one (z, t) plane:
+//   part[plane][(n_x, n_y)][f] = sum_{x,y} F_f(x, y) e^{-2 pi i (n_x x / Lx + n_y y / Ly)}
+// in chunks of nfc fields (a divisor of 160 sized to shared memory).  x: one thread per (field, row) reads the row
+// once from global memory and keeps XY_NC momenta in flight; y: one thread
+// per (field, n_x) over the rows in shared memory; the chunk's results are
+// staged so that the stores run along f.
+template <typename R>
+__global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __restrict__ F, Geom g, int rad,
+                                                            int nfc, double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lx = a.g.L[0], ly = a.g.L[1], lz = a.g.L[2];
+  const int lx = g.L[0], ly = g.L[1];
+  const int nx = 2 * rad + 1, nxy = nx * nx;
   const int plane = blockIdx.x;  // z + Lz * t
-  const int z = plane % lz, t = plane / lz;
-  const int nx = a.nx, nxy = nx * nx, rb = a.rb;
-  cplx<R>* F = reinterpret_cast<cplx<R>*>(smem_raw);  // [rb*lx][FSTR]
-  cplx<R>* X = F + (size_t)rb * lx * FSTR;            // [rb][nx][NF]
-  cplx<R>* Y = X + (size_t)rb * nx * NF;              // [nxy][NF]
-  cplx<R>* twx = Y + (size_t)nxy * NF;                // [nx][lx]
-  cplx<R>* twy = twx + (size_t)nx * lx;               // [nx][ly]
+  cplx<R>* X = reinterpret_cast<cplx<R>*>(smem_raw);  // [nfc][ly][nx]
+  cplx<R>* Y = X + (size_t)nfc * ly * nx;            // [nxy][nfc]
+  cplx<R>* twx = Y + (size_t)nxy * nfc;              // [lx][nx]
+  cplx<R>* twy = twx + (size_t)lx * nx;                // [ly][nx]
   for (int k = threadIdx.x; k < nx * lx; k += blockDim.x) {
-    const int n = k / lx - a.rad, x = k % lx;
+    const int x = k / nx, n = k % nx - rad;
     twiddle(twx[k], ((n * x) % lx + lx) % lx, lx);
   }
   for (int k = threadIdx.x; k < nx * ly; k += blockDim.x) {
-    const int n = k / ly - a.rad, y = k % ly;
+    const int y = k / nx, n = k % nx - rad;
     twiddle(twy[k], ((n * y) % ly + ly) % ly, ly);
   }
-  for (int pass = 0; pass < 5; ++pass) {
-    for (int k = threadIdx.x; k < NF * nxy; k += blockDim.x) Y[k] = mk<R>(0, 0);
-    for (int y0 = 0; y0 < ly; y0 += rb) {
-      const int rows = min(rb, ly - y0);
-      __syncthreads();
-      for (int sidx = threadIdx.x; sidx < rows * lx; sidx += blockDim.x) {
-        const int x = sidx % lx, y = y0 + sidx / lx;
-        const int c[4] = {x, y, z, t};
-        const int i = x + lx * (y + ly * (z + lz * t));
-        cplx<R> acc[NF];
-        site_fields<R, PS, PL>(acc, a, pass, i, c);
+  const size_t V = (size_t)g.V;
+  const cplx<R>* Fp = F + (size_t)plane * lx * ly;
+  for (int f0 = 0; f0 < 5 * NF; f0 += nfc) {
+    __syncthreads();
+    for (int task = threadIdx.x; task < nfc * ly; task += blockDim.x) {
+      const int row = task % ly, f = task / ly;
+      const cplx<R>* src = Fp + (size_t)(f0 + f) * V + (size_t)row * lx;
+      cplx<R>* dst = X + ((size_t)f * ly + row) * nx;
+      for (int n0 = 0; n0 < nx; n0 += XY_NC) {
+        cplx<R> acc[XY_NC];
 #pragma unroll
-        for (int f = 0; f < NF; ++f) F[(size_t)sidx * FSTR + f] = acc[f];
-      }
-      __syncthreads();
-      // x transform: X[row][n][f] = sum_x F[row*lx + x][f] e^{-2 pi i n x / lx}
-      for (int k = threadIdx.x; k < NF * rows * nx; k += blockDim.x) {
-        const int f = k % NF, rn = k / NF, n = rn % nx, row = rn / nx;
-        cplx<R> sum = mk<R>(0, 0);
-        for (int x = 0; x < lx; ++x) cmac(sum, F[((size_t)row * lx + x) * FSTR + f], twx[n * lx + x]);
-        X[((size_t)row * nx + n) * NF + f] = sum;
-      }
-      __syncthreads();
-      // y transform, accumulated over row blocks: Y[(n_x, n_y)][f]
-      for (int k = threadIdx.x; k < NF * nxy; k += blockDim.x) {
-        const int f = k % NF, nn = k / NF, n_x = nn / nx, n_y = nn % nx;
-        cplx<R> sum = Y[k];
-        for (int row = 0; row < rows; ++row)
-          cmac(sum, X[((size_t)row * nx + n_x) * NF + f], twy[n_y * ly + y0 + row]);
-        Y[k] = sum;
+        for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+        for (int x = 0; x < lx; ++x) {
+          const cplx<R> v = src[x];
+          const cplx<R>* tw = twx + (size_t)x * nx + n0;
+#pragma unroll
+          for (int j = 0; j < XY_NC; ++j)
+            if (n0 + j < nx) cmac(acc[j], v, tw[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < XY_NC; ++j)
+          if (n0 + j < nx) dst[n0 + j] = acc[j];
       }
     }
     __syncthreads();
-    // part layout [plane][nxy][160]
-    for (int k = threadIdx.x; k < NF * nxy; k += blockDim.x) {
-      const int f = k % NF, nn = k / NF;
-      a.part[((size_t)plane * nxy + nn) * 160 + pass * NF + f] = make_double2((double)Y[k].re, (double)Y[k].im);
+    for (int task = threadIdx.x; task < nfc * nx; task += blockDim.x) {
+      const int f = task % nfc, n_x = task / nfc;
+      const cplx<R>* src = X + (size_t)f * ly * nx + n_x;
+      for (int n0 = 0; n0 < nx; n0 += XY_NC) {
+        cplx<R> acc[XY_NC];
+#pragma unroll
+        for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+        for (int row = 0; row < ly; ++row) {
+          const cplx<R> v = src[(size_t)row * nx];
+          const cplx<R>* tw = twy + (size_t)row * nx + n0;
+#pragma unroll
+          for (int j = 0; j < XY_NC; ++j)
+            if (n0 + j < nx) cmac(acc[j], v, tw[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < XY_NC; ++j)
+          if (n0 + j < nx) Y[((size_t)n_x * nx + n0 + j) * nfc + f] = acc[j];
+      }
     }
     __syncthreads();
+    for (int k = threadIdx.x; k < nxy * nfc; k += blockDim.x) {
+      const int f = k % nfc, nn = k / nfc;
+      part[((size_t)plane * nxy + nn) * 160 + f0 + f] = make_double2((double)Y[k].re, (double)Y[k].im);
+    }
   }
 }
 
-// z transform (FP64) and Gamma insertions.  Block (t, group): group = 2 pass + k
-// holds one 4x4 matrix field (16 fields).
+// z transform (FP64), the derivative shift and the Gamma insertions.  Block
+// (t, group): group = 2 pass + k holds one 4x4 matrix field (16 fields).
 __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restrict__ part, const int* __restrict__ mom,
-                                                         int n_mom, int lz, int lt, int rad, int nx, double mup,
-                                                         double* out, int accumulate) {
+                                                         int n_mom, Geom g, int rad, double mup, double* out,
+                                                         int accumulate) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lz = g.L[2], lt = g.L[3];
   const int t = blockIdx.x, group = blockIdx.y;
   const int pass = group >> 1, k = group & 1;
-  const int nxy = nx * nx;
+  const int nx = 2 * rad + 1, nxy = nx * nx;
   double2* zs = reinterpret_cast<double2*>(smem_raw);  // [n_mom][16]
   double2* twz = zs + (size_t)n_mom * 16;               // [nx][lz]
   for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
@@ -304,16 +325,32 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
   }
   __syncthreads();
   const int field0 = pass * NF + k * 16;
+  const int tm1 = (t + lt - 1) % lt;
   for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
     const int m = q / 16, e = q % 16;
     const int mx = mom[3 * m], my = mom[3 * m + 1], mz = mom[3 * m + 2];
     const int nn = (mx + rad) * nx + (my + rad);
     double re = 0.0, im = 0.0;
     for (int zz = 0; zz < lz; ++zz) {
-      const double2 p = part[((size_t)(zz + lz * t) * nxy + nn) * 160 + field0 + e];
+      double2 p = part[((size_t)(zz + lz * t) * nxy + nn) * 160 + field0 + e];
+      if (pass == 4) {  // O_t(t) = D_t(t) + D_t(t - 1)
+        const double2 p1 = part[((size_t)(zz + lz * tm1) * nxy + nn) * 160 + field0 + e];
+        p.x += p1.x;
+        p.y += p1.y;
+      }
       const double2 w = twz[(mz + rad) * lz + zz];
       re += p.x * w.x - p.y * w.y;
       im += p.x * w.y + p.y * w.x;
+    }
+    if (pass >= 1 && pass <= 3) {  // O_mu(p) = (1 + e^{-2 pi i n_mu / L_mu}) D_mu(p)
+      const int nmu = pass == 1 ? mx : (pass == 2 ? my : mz);
+      const int L = g.L[pass - 1];
+      double sn, cs;
+      sincospi(2.0 * (double)(((nmu % L) + L) % L) / (double)L, &sn, &cs);
+      const double fr = 1.0 + cs, fi = -sn;
+      const double r2 = re * fr - im * fi, i2 = re * fi + im * fr;
+      re = r2;
+      im = i2;
     }
     zs[q] = make_double2(re, im);
   }
@@ -347,7 +384,7 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
 }  // namespace
 
 struct ContractWorkspace {
-  DevBuf v, part, mom;
+  DevBuf v, fields, part, mom;
   bool gamma_ready = false;
 };
 
@@ -355,32 +392,43 @@ void ContractWsDeleter::operator()(ContractWorkspace* w) const { delete w; }
 
 namespace {
 
+size_t xy_smem(const Geom& g, int rad, int nfc, size_t cs) {
+  const int nx = 2 * rad + 1;
+  return cs * ((size_t)nfc * g.L[1] * nx + (size_t)nx * nx * nfc + (size_t)nx * (g.L[0] + g.L[1]));
+}
+
+// Largest chunk of fields (dividing 160) whose transform fits in 160 KB; 0 if none.
+int xy_chunk(const Geom& g, int rad, size_t cs) {
+  for (int nfc : {32, 16, 8, 4, 2, 1})
+    if (xy_smem(g, rad, nfc, cs) <= 160 * 1024) return nfc;
+  return 0;
+}
+
+// Site fields then x/y transform; F holds 160 V fields of type cplx<R>.
 template <typename R, int PS, int PL>
-int launch_planes(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsrc, int rad, double2* part,
-                  cudaStream_t st) {
-  ContractArgs<R> a;
+int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsrc, int rad, void* F, double2* part,
+                     cudaStream_t st, EventPair* ev_f, EventPair* ev_xy) {
+  FieldArgs<R> a;
   a.g = g->geom;
   a.s = s_dev;
   a.v = v_dev;
   a.links = g->links[PL].p;
   a.nsrc = nsrc;
-  a.rad = rad;
-  a.nx = 2 * rad + 1;
-  a.part = part;
-  const int lx = g->geom.L[0], ly = g->geom.L[1];
-  const size_t cs = sizeof(cplx<R>);
-  const size_t fixed = (size_t)NF * a.nx * a.nx * cs + (size_t)a.nx * (lx + ly) * cs;
-  const size_t per_row = (size_t)lx * FSTR * cs + (size_t)NF * a.nx * cs;
-  const size_t budget = 160 * 1024;
-  if (fixed + per_row > budget) return fail(TSM_ERR_INVALID_ARG, "plane %dx%d too large for the contraction", lx, ly);
-  int rb_max = (int)std::min<size_t>((size_t)ly, (budget - fixed) / per_row);
-  const int nrb = (ly + rb_max - 1) / rb_max;
-  a.rb = (ly + nrb - 1) / nrb;
-  const size_t smem = fixed + per_row * a.rb;
-  auto kern = contract_plane_kernel<R, PS, PL>;
+  a.F = static_cast<cplx<R>*>(F);
+  const int nfc = xy_chunk(g->geom, rad, sizeof(cplx<R>));
+  if (nfc == 0)
+    return fail(TSM_ERR_INVALID_ARG, "plane %dx%d too large for the contraction", g->geom.L[0], g->geom.L[1]);
+  const size_t smem = xy_smem(g->geom, rad, nfc, sizeof(cplx<R>));
+  const unsigned nblk = (unsigned)((g->geom.V + FLD_BS - 1) / FLD_BS);
+  count_launches(2);
+  if (ev_f) TSM_TRY(ev_f->begin(st));
+  contract_fields_kernel<R, PS, PL><<<nblk * 5, FLD_BS, 0, st>>>(a);
+  if (ev_f) TSM_TRY(ev_f->end(st));
+  auto kern = contract_xy_kernel<R>;
   TSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  count_launches(1);
-  kern<<<g->geom.L[2] * g->geom.L[3], K4_BS, smem, st>>>(a);
+  if (ev_xy) TSM_TRY(ev_xy->begin(st));
+  kern<<<g->geom.L[2] * g->geom.L[3], XY_BS, smem, st>>>(a.F, g->geom, rad, nfc, part);
+  if (ev_xy) TSM_TRY(ev_xy->end(st));
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }
@@ -411,44 +459,50 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
   const int V = g->geom.V;
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2], lt = g->geom.L[3];
+  const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
   TSM_TRY(w.v.reserve((size_t)nsrc * spinor_chunks(prec) * V * 16));
+  TSM_TRY(w.fields.reserve((size_t)160 * V * cs));
   TSM_TRY(w.part.reserve((size_t)lz * lt * 160 * nx * nx * sizeof(double2)));
   TSM_TRY(w.mom.reserve(sizeof(int) * 3 * (size_t)std::max(n_mom, 1)));
   TSM_CUDA(cudaMemcpyAsync(w.mom.p, mom_host, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, st));
   const bool prof = profiling();
-  EventPair ev_v, ev_p, ev_z;
+  EventPair ev_v, ev_f, ev_xy, ev_z;
   // v = g5 A s
   if (prof) TSM_TRY(ev_v.begin(st));
   TSM_TRY(dslash_apply_mixed(g, prec, prec, TSM_OP_A, kappa, 0.0, s_dev, w.v.p, nsrc, 1, st));
   if (prof) TSM_TRY(ev_v.end(st));
-  if (prof) TSM_TRY(ev_p.begin(st));
   if (prec == TSM_F32)
-    TSM_TRY((launch_planes<float, TSM_F32, TSM_F32>(g, s_dev, w.v.p, nsrc, rad, w.part.as<double2>(), st)));
+    TSM_TRY((launch_fields_xy<float, TSM_F32, TSM_F32>(g, s_dev, w.v.p, nsrc, rad, w.fields.p, w.part.as<double2>(),
+                                                        st, prof ? &ev_f : nullptr, prof ? &ev_xy : nullptr)));
   else
-    TSM_TRY((launch_planes<double, TSM_F64, TSM_F64>(g, s_dev, w.v.p, nsrc, rad, w.part.as<double2>(), st)));
-  if (prof) TSM_TRY(ev_p.end(st));
+    TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, w.v.p, nsrc, rad, w.fields.p,
+                                                         w.part.as<double2>(), st, prof ? &ev_f : nullptr,
+                                                         prof ? &ev_xy : nullptr)));
   const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
   TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   if (prof) TSM_TRY(ev_z.begin(st));
   count_launches(1);
-  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), n_mom, lz, lt, rad, nx,
+  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), n_mom, g->geom, rad,
                                                       2.0 * kappa * mu, out_dev, accumulate);
   if (prof) TSM_TRY(ev_z.end(st));
   TSM_CUDA(cudaGetLastError());
   if (prof) {
     const double v = (double)V, n = (double)nsrc, b = spinor_site_bytes(prec), l = link_site_bytes(prec);
     const double part_bytes = (double)lz * lt * nx * nx * 160 * 16;
+    const double field_bytes = 160.0 * v * (double)cs;
     const double out_bytes = 160.0 * n_mom * lt * 16 * (accumulate ? 2 : 1);
     const char* pn = prec == TSM_F32 ? "f32" : "f64";
     char name[48];
     snprintf(name, sizeof(name), "contract_g5A_%s", pn);
     prof_add(name, ev_v.seconds(), v * (l + 2 * n * b), v * n * 1392.0);
-    // per site and source: 4 x (4 colour matvecs x 4 spins + 4 outer products) + 2 outer products;
-    // per site and batch: x transform of 160 fields + y transform share
-    const double cmac_src = 4 * (16 * 9 + 4 * 48) + 2 * 48;
+    // per site and source: 4 x (2 colour matvecs x 4 spins + 3 outer products) + 2 outer products
+    const double cmac_src = 4 * (2 * 36 + 3 * 48) + 2 * 48;
+    snprintf(name, sizeof(name), "contract_fields_%s", pn);
+    prof_add(name, ev_f.seconds(), v * (l + 2 * n * b) + field_bytes, 8.0 * v * n * cmac_src);
+    // x transform of 160 fields (nx momenta) + y transform (nx^2 momenta, per row)
     const double cmac_dft = 160.0 * nx + 160.0 * nx * nx / g->geom.L[0];
-    snprintf(name, sizeof(name), "contract_plane_%s", pn);
-    prof_add(name, ev_p.seconds(), v * (l + 2 * n * b) + part_bytes, 8.0 * v * (n * cmac_src + cmac_dft));
+    snprintf(name, sizeof(name), "contract_xy_%s", pn);
+    prof_add(name, ev_xy.seconds(), field_bytes + part_bytes, 8.0 * v * cmac_dft);
     snprintf(name, sizeof(name), "contract_project_z");
     prof_add(name, ev_z.seconds(), part_bytes + out_bytes, 8.0 * 160.0 * n_mom * lt * lz + 8.0 * 160 * n_mom * lt);
   }
@@ -511,31 +565,37 @@ int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, cons
   const int V = g->geom.V;
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2], lt = g->geom.L[3];
+  const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
   const size_t mom_bytes = round256(sizeof(int) * 3 * (size_t)n_mom);
   const size_t v_bytes = round256((size_t)nsrc * spinor_chunks(prec) * V * 16);
+  const size_t f_bytes = round256((size_t)160 * V * cs);
   const size_t part_bytes = round256((size_t)lz * lt * 160 * nx * nx * sizeof(double2));
-  const size_t need = mom_bytes + v_bytes + part_bytes;
+  const size_t need = mom_bytes + v_bytes + f_bytes + part_bytes;
   if (need > (size_t)TSM_CONTRACT_NOALLOC_MAX_BYTES)
     return fail(TSM_ERR_INVALID_ARG,
-                "tsm_contract_loops_noalloc needs %zu scratch bytes (fields %zu + partial sums %zu), above the "
-                "fixed %d; use fewer sources per call, a smaller momentum radius or tsm_contract_loops",
-                need, v_bytes, part_bytes, (int)TSM_CONTRACT_NOALLOC_MAX_BYTES);
+                "tsm_contract_loops_noalloc needs %zu scratch bytes (solutions %zu + site fields %zu + partial sums "
+                "%zu), above the fixed %d; use fewer sources per call, a smaller momentum radius or "
+                "tsm_contract_loops",
+                need, v_bytes, f_bytes, part_bytes, (int)TSM_CONTRACT_NOALLOC_MAX_BYTES);
   unsigned char* base = nullptr;
   TSM_TRY(noalloc_setup(g->ctx->device, &base));
   int* mom_dev = reinterpret_cast<int*>(base);
   void* v_dev = base + mom_bytes;
-  double2* part = reinterpret_cast<double2*>(base + mom_bytes + v_bytes);
+  void* f_dev = base + mom_bytes + v_bytes;
+  double2* part = reinterpret_cast<double2*>(base + mom_bytes + v_bytes + f_bytes);
   TSM_CUDA(cudaMemcpyAsync(mom_dev, mom_host, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, st));
   TSM_TRY(dslash_apply_fixed(g, prec, TSM_OP_A, kappa, 0.0, s_dev, v_dev, nsrc, 1, 1, st));
   if (prec == TSM_F32)
-    TSM_TRY((launch_planes<float, TSM_F32, TSM_F32>(g, s_dev, v_dev, nsrc, rad, part, st)));
+    TSM_TRY((launch_fields_xy<float, TSM_F32, TSM_F32>(g, s_dev, v_dev, nsrc, rad, f_dev, part, st, nullptr,
+                                                        nullptr)));
   else
-    TSM_TRY((launch_planes<double, TSM_F64, TSM_F64>(g, s_dev, v_dev, nsrc, rad, part, st)));
+    TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, v_dev, nsrc, rad, f_dev, part, st, nullptr,
+                                                         nullptr)));
   const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
   TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   count_launches(1);
-  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(part, mom_dev, n_mom, lz, lt, rad, nx, 2.0 * kappa * mu,
-                                                      out_dev, accumulate);
+  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(part, mom_dev, n_mom, g->geom, rad, 2.0 * kappa * mu, out_dev,
+                                                      accumulate);
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }

@@ -90,7 +90,7 @@ int tuned_nr(tsm_gauge* g, int pin, int pl, int nrhs, cudaStream_t s, int* nr) {
     *nr = forced;
     return TSM_OK;
   }
-  if (nrhs <= 1) {
+  if (nrhs <= 1 || pin == TSM_DS) {  // float-float sums leave no registers for a second right-hand side
     *nr = 1;
     return TSM_OK;
   }

@@ -22,16 +22,20 @@ namespace tsm {
 
 constexpr int DSLASH_BS = 128;
 
-// Resident blocks per SM the register allocation must allow (__launch_bounds__):
-// FP32 fields measured fastest at 6 (<= 80 registers); the other kernels keep
-// the compiler's choice.
+// Resident blocks per SM the register allocation must allow (__launch_bounds__),
+// per field precision: FP32 measured fastest at 6 (<= 80 registers), 16-bit
+// fields at 6 (<= 80 registers); FP64 and float-float keep the compiler's
+// choice.  TSM_DSLASH_MINB32 / TSM_DSLASH_MINB16 override (variant builds).
+#ifndef TSM_DSLASH_MINB32
+#define TSM_DSLASH_MINB32 6
+#endif
+#ifndef TSM_DSLASH_MINB16
+#define TSM_DSLASH_MINB16 6
+#endif
 template <int PIN>
 struct MinBlocks {
-#ifdef TSM_DSLASH_MINB
-  static constexpr int value = TSM_DSLASH_MINB;
-#else
-  static constexpr int value = (PIN == TSM_F32) ? 6 : 1;
-#endif
+  static constexpr int value =
+      (PIN == TSM_F32) ? TSM_DSLASH_MINB32 : ((PIN == TSM_F16 || PIN == TSM_BF16) ? TSM_DSLASH_MINB16 : 1);
 };
 
 struct DslashArgs {
@@ -43,6 +47,7 @@ struct DslashArgs {
   double kappa;
   double tw;          // twist coefficient multiplying i g5
   float kappa_f, tw_f;  // the same, pre-rounded for FP32 kernels (no per-thread FP64 conversion)
+  dsf kappa_ds, tw_ds;  // and split into float pairs for float-float kernels
   // checkerboarded operator (even-odd kernels only):
   //   out(j) = (c0 + i c1 g5) center(j) + (h0 + i h1 g5) hop(in)(j)
   // on the sites of parity `parity`, j = full site >> 1; center may be null.
@@ -50,6 +55,7 @@ struct DslashArgs {
   int parity;
   double c0, c1, h0, h1;
   float c0_f, c1_f, h0_f, h1_f;
+  dsf c0_ds, c1_ds, h0_ds, h1_ds;
 };
 
 __host__ __device__ inline void set_eo(DslashArgs& a, const void* center, int parity, double c0, double c1, double h0,
@@ -64,6 +70,10 @@ __host__ __device__ inline void set_eo(DslashArgs& a, const void* center, int pa
   a.c1_f = (float)c1;
   a.h0_f = (float)h0;
   a.h1_f = (float)h1;
+  a.c0_ds = dsf(c0);
+  a.c1_ds = dsf(c1);
+  a.h0_ds = dsf(h0);
+  a.h1_ds = dsf(h1);
 }
 
 template <typename R>
@@ -75,6 +85,15 @@ struct EoCoef<float> {
     c1 = a.c1_f;
     h0 = a.h0_f;
     h1 = a.h1_f;
+  }
+};
+template <>
+struct EoCoef<dsf> {
+  __device__ static void get(const DslashArgs& a, dsf& c0, dsf& c1, dsf& h0, dsf& h1) {
+    c0 = a.c0_ds;
+    c1 = a.c1_ds;
+    h0 = a.h0_ds;
+    h1 = a.h1_ds;
   }
 };
 template <>
@@ -93,18 +112,24 @@ template <>
 __device__ __forceinline__ float arg_kappa<float>(const DslashArgs& a) { return a.kappa_f; }
 template <>
 __device__ __forceinline__ double arg_kappa<double>(const DslashArgs& a) { return a.kappa; }
+template <>
+__device__ __forceinline__ dsf arg_kappa<dsf>(const DslashArgs& a) { return a.kappa_ds; }
 template <typename R>
 __device__ __forceinline__ R arg_tw(const DslashArgs& a);
 template <>
 __device__ __forceinline__ float arg_tw<float>(const DslashArgs& a) { return a.tw_f; }
 template <>
 __device__ __forceinline__ double arg_tw<double>(const DslashArgs& a) { return a.tw; }
+template <>
+__device__ __forceinline__ dsf arg_tw<dsf>(const DslashArgs& a) { return a.tw_ds; }
 
 __host__ __device__ inline void set_coeffs(DslashArgs& a, double kappa, double tw) {
   a.kappa = kappa;
   a.tw = tw;
   a.kappa_f = (float)kappa;
   a.tw_f = (float)tw;
+  a.kappa_ds = dsf(kappa);
+  a.tw_ds = dsf(tw);
 }
 
 struct RedSlots {
@@ -478,11 +503,22 @@ __global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_eo_ke
   dslash_block_eo<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
 }
 
-// a.nblk must be ceil(V/2 / DSLASH_BS).  One right-hand side per thread.
+// a.nblk must be ceil(V/2 / DSLASH_BS); nr right-hand sides per thread (1, 2
+// or 4; 4 only for FP32 sums).
 template <typename R, int SF, int PIN, int PL, class Epi>
-inline void launch_dslash_eo(const DslashArgs& a, const Epi& e, cudaStream_t s) {
-  const unsigned grid = (unsigned)a.nblk * (unsigned)a.nrhs;
-  dslash_eo_kernel<R, SF, PIN, PL, 1, Epi><<<grid, DSLASH_BS, 0, s>>>(a, e);
+inline void launch_dslash_eo(int nr, const DslashArgs& a, const Epi& e, cudaStream_t s) {
+  const unsigned nb = (unsigned)a.nblk;
+  if constexpr (sizeof(R) == 4) {
+    if (nr == 4) {
+      dslash_eo_kernel<R, SF, PIN, PL, 4, Epi><<<nb * (unsigned)((a.nrhs + 3) / 4), DSLASH_BS, 0, s>>>(a, e);
+      return;
+    }
+  }
+  if (nr >= 2) {
+    dslash_eo_kernel<R, SF, PIN, PL, 2, Epi><<<nb * (unsigned)((a.nrhs + 1) / 2), DSLASH_BS, 0, s>>>(a, e);
+  } else {
+    dslash_eo_kernel<R, SF, PIN, PL, 1, Epi><<<nb * (unsigned)a.nrhs, DSLASH_BS, 0, s>>>(a, e);
+  }
 }
 
 // Plain store of the result (optionally times g5), no reduction.

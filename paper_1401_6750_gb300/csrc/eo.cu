@@ -86,6 +86,7 @@ struct EoWorkspace {
   int* h_mask = nullptr;
   std::map<int, cudaGraphExec_t> graphs;
   double graph_kappa = 0.0, graph_mup = 0.0;
+  int nr_s = 1, nr_p = 1;  // right-hand sides per thread (sloppy, precise operator)
   ~EoWorkspace() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
     if (h_st) cudaFreeHost(h_st);
@@ -95,6 +96,23 @@ struct EoWorkspace {
 void EoWsDeleter::operator()(EoWorkspace* w) const { delete w; }
 
 namespace {
+
+// Right-hand sides per thread of the checkerboarded operator on fields of
+// precision `prec`; TSM_EO_NR_<F64|F32|F16|BF16> override it (measurements).
+int eo_nr(int prec) {
+  if (prec == TSM_DS) return 1;  // float-float sums leave no registers for a second right-hand side
+  static const int env[4] = {
+      [] { const char* e = getenv("TSM_EO_NR_F64"); return e ? atoi(e) : 0; }(),
+      [] { const char* e = getenv("TSM_EO_NR_F32"); return e ? atoi(e) : 0; }(),
+      [] { const char* e = getenv("TSM_EO_NR_F16"); return e ? atoi(e) : 0; }(),
+      [] { const char* e = getenv("TSM_EO_NR_BF16"); return e ? atoi(e) : 0; }(),
+  };
+  static const int dflt[4] = {1, 1, 1, 1};
+  int nr = (prec >= 0 && prec < 4 && env[prec]) ? env[prec] : dflt[prec & 3];
+  if (nr != 1 && nr != 2 && nr != 4) nr = 1;
+  if (nr == 4 && prec == TSM_F64) nr = 2;
+  return nr;
+}
 
 int eo_chunk() {
   static int k = [] {
@@ -133,7 +151,7 @@ struct SolverEO {
     TSM_TRY(w.p.reserve(half(T::PS, V, nrhs)));
     TSM_TRY(w.q.reserve(half(T::PS, V, nrhs)));
     TSM_TRY(w.tes.reserve(half(T::PS, V, nrhs)));
-    if (T::XACC) TSM_TRY(w.xacc.reserve(half(TSM_F64, V, nrhs)));
+    if (T::XACC) TSM_TRY(w.xacc.reserve(half(T::PXA, V, nrhs)));
     TSM_TRY(w.full.reserve(2 * half(T::PP, V, nrhs)));
     if (w.h_st) cudaFreeHost(w.h_st);
     if (w.h_mask) cudaFreeHost(w.h_mask);
@@ -186,16 +204,16 @@ struct SolverEO {
     const size_t Vh = (size_t)g->geom.V / 2;
     EpiStore<Rs, T::PS> es{w.tes.p, Vh, 0, RedSlots{nullptr, nullptr}};
     // q = Mhat p
-    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
+    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
     {
       EpiMp<Rs, T::PS> e{w.q.p, Vh, w.st.as<RhsState>(), slots(w)};
-      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
+      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
     }
     // Ap = Mhat^dag q; r -= alpha Ap; x += alpha p
-    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
+    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, Vh, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
     }
     dim3 eg(((int)Vh + EW_BS - 1) / EW_BS, nrhs);
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 0, (int)Vh);
@@ -215,21 +233,21 @@ struct SolverEO {
     EpiStore<Rs, T::PS> es{w.tes.p, Vh, 0, RedSlots{nullptr, nullptr}};
     EventPair ev[5];
     TSM_TRY(ev[0].begin(s));
-    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
+    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
     TSM_TRY(ev[0].end(s));
     TSM_TRY(ev[1].begin(s));
     {
       EpiMp<Rs, T::PS> e{w.q.p, Vh, w.st.as<RhsState>(), slots(w)};
-      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
+      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
     }
     TSM_TRY(ev[1].end(s));
     TSM_TRY(ev[2].begin(s));
-    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
+    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
     TSM_TRY(ev[2].end(s));
     TSM_TRY(ev[3].begin(s));
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, Vh, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
     }
     TSM_TRY(ev[3].end(s));
     TSM_TRY(ev[4].begin(s));
@@ -289,18 +307,18 @@ struct SolverEO {
     const void* xs = w.x.p;
     count_launches(T::XACC ? 6 : 5);
     if (T::XACC) {
-      k_fold<T::PA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.mask.as<int>(), (int)Vh);
+      k_fold<T::PA, T::PXA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.p, w.mask.as<int>(), (int)Vh);
       xs = w.xacc.p;
     }
     const int* m = w.mask.as<int>();
     EpiStoreMasked<Rp, T::PP> to_tep{w.tep.p, Vh, m, RedSlots{nullptr, nullptr}};
     EpiStoreMasked<Rp, T::PP> to_t1{w.t1.p, Vh, m, RedSlots{nullptr, nullptr}};
-    launch_dslash_eo<Rp, -1, T::PX, T::PLp>(step_a(g, T::PLp, xs, kappa, mup, nrhs), to_tep, s);
-    launch_dslash_eo<Rp, -1, T::PP, T::PLp>(step_b(g, T::PLp, w.tep.p, xs, kappa, mup, nrhs), to_t1, s);
-    launch_dslash_eo<Rp, +1, T::PP, T::PLp>(step_a(g, T::PLp, w.t1.p, kappa, -mup, nrhs), to_tep, s);
+    launch_dslash_eo<Rp, -1, T::PX, T::PLp>(w.nr_p, step_a(g, T::PLp, xs, kappa, mup, nrhs), to_tep, s);
+    launch_dslash_eo<Rp, -1, T::PP, T::PLp>(w.nr_p, step_b(g, T::PLp, w.tep.p, xs, kappa, mup, nrhs), to_t1, s);
+    launch_dslash_eo<Rp, +1, T::PP, T::PLp>(w.nr_p, step_a(g, T::PLp, w.t1.p, kappa, -mup, nrhs), to_tep, s);
     {
       EpiResidual<Rp, T::PP, T::PA> e{w.b.p, w.r.p, Vh, m, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(step_b(g, T::PLp, w.tep.p, w.t1.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(w.nr_p, step_b(g, T::PLp, w.tep.p, w.t1.p, kappa, -mup, nrhs), e, s);
     }
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 1, (int)Vh);
     TSM_CUDA(cudaGetLastError());
@@ -316,23 +334,32 @@ struct SolverEO {
     const int V = g->geom.V;
     const size_t Vh = (size_t)V / 2;
     dim3 fg((V + EW_BS - 1) / EW_BS, nrhs), eg(((int)Vh + EW_BS - 1) / EW_BS, nrhs);
+    {
+      const int nr_s = eo_nr(T::PS), nr_p = eo_nr(T::PP);
+      if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
+        for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
+        w.graphs.clear();
+      }
+      w.nr_s = nr_s;
+      w.nr_p = nr_p;
+    }
     count_launches(7);
     // split eta; t1 = eta_o, tep = M_ee^{-1} eta_e
     k_gather_eo<T::PP><<<fg, EW_BS, 0, s>>>(w.full.p, w.eta_e.p, w.t1.p, g->geom);
     k_diag<T::PP><<<eg, EW_BS, 0, s>>>(w.tep.p, w.eta_e.p, 1.0 / d, -mup / d, (int)Vh);
     {  // t1 = eta_o - M_oe M_ee^{-1} eta_e = eta_o + kappa H tep   (in place on t1)
       EpiStore<Rp, T::PP> e{w.t1.p, Vh, 0, RedSlots{nullptr, nullptr}};
-      launch_dslash_eo<Rp, -1, T::PP, T::PLp>(args(g, T::PLp, w.tep.p, w.t1.p, 1, kappa, 1.0, 0.0, kappa, 0.0, nrhs),
+      launch_dslash_eo<Rp, -1, T::PP, T::PLp>(w.nr_p, args(g, T::PLp, w.tep.p, w.t1.p, 1, kappa, 1.0, 0.0, kappa, 0.0, nrhs),
                                               e, s);
     }
     {  // b = Mhat^dag t1, state initialisation
       EpiStore<Rp, T::PP> e{w.tep.p, Vh, 0, RedSlots{nullptr, nullptr}};
-      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(step_a(g, T::PLp, w.t1.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(w.nr_p, step_a(g, T::PLp, w.t1.p, kappa, -mup, nrhs), e, s);
       EpiInitB<Rp, T::PP> ei{w.b.p, Vh, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(step_b(g, T::PLp, w.tep.p, w.t1.p, kappa, -mup, nrhs), ei, s);
+      launch_dslash_eo<Rp, +1, T::PP, T::PLp>(w.nr_p, step_b(g, T::PLp, w.tep.p, w.t1.p, kappa, -mup, nrhs), ei, s);
     }
-    k_init<T::PP, T::PA, T::PS, T::XACC>
-        <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.as<double2>(), w.st.as<RhsState>(), (int)Vh);
+    k_init<T::PP, T::PA, T::PS, T::XACC, T::PXA>
+        <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.p, w.st.as<RhsState>(), (int)Vh);
     TSM_CUDA(cudaGetLastError());
     const long long limit = (long long)max_iter / eo_chunk() + 64;
     for (long long round = 0;; ++round) {
@@ -364,10 +391,10 @@ struct SolverEO {
     }
     // s_o = x (+ xacc) into t1; s_e = M_ee^{-1} (eta_e + kappa H s_o) into tep; scatter
     count_launches(3);
-    k_output<T::PA, T::PP, T::XACC><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.t1.p, 0, (int)Vh);
+    k_output<T::PA, T::PP, T::XACC, T::PXA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.p, w.t1.p, 0, (int)Vh);
     {
       EpiStore<Rp, T::PP> e{w.tep.p, Vh, 0, RedSlots{nullptr, nullptr}};
-      launch_dslash_eo<Rp, -1, T::PP, T::PLp>(
+      launch_dslash_eo<Rp, -1, T::PP, T::PLp>(w.nr_p, 
           args(g, T::PLp, w.t1.p, w.eta_e.p, 0, kappa, 1.0 / d, -mup / d, kappa / d, -kappa * mup / d, nrhs), e, s);
     }
     switch (out_prec) {

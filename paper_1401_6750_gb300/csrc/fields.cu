@@ -18,6 +18,18 @@ __global__ void pack_links_f64(const double2* __restrict__ src, double2* __restr
     for (int k = 0; k < 9; ++k) dst[((size_t)mu * 9 + k) * V + i] = src[((size_t)i * 4 + mu) * 9 + k];
 }
 
+// float-float copy of the FP64 links (precise operator of the reliable-update solver)
+__global__ void pack_links_ds(const double2* __restrict__ src, float4* __restrict__ dst, int V) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= V) return;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int k = 0; k < 9; ++k) {
+      const double2 u = src[((size_t)i * 4 + mu) * 9 + k];
+      const dsf a(u.x), b(u.y);
+      dst[((size_t)mu * 9 + k) * V + i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+}
+
 __global__ void pack_links_f32(const double2* __restrict__ src, float4* __restrict__ dst, int V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
@@ -137,6 +149,7 @@ int convert_from(int ps, void* dst, const void* src, int V, int nrhs, int gamma5
     case TSM_F32: convert_kernel<PD, TSM_F32><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
     case TSM_F16: convert_kernel<PD, TSM_F16><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
     case TSM_BF16: convert_kernel<PD, TSM_BF16><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
+    case TSM_DS: convert_kernel<PD, TSM_DS><<<grid, BS, 0, s>>>(dst, src, V, gamma5); break;
     default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", ps);
   }
   TSM_CUDA(cudaGetLastError());
@@ -152,7 +165,9 @@ int build_links(tsm_gauge* g, const double* links_host) {
   TSM_TRY(staging.reserve(host_bytes));
   TSM_CUDA(cudaMemcpy(staging.p, links_host, host_bytes, cudaMemcpyHostToDevice));
   const int nb = (V + BS - 1) / BS;
-  for (int p = 0; p < 4; ++p) {
+  // an FP64 copy comes with its float-float twin
+  if (has_prec(g, TSM_F64)) g->precisions |= 1u << TSM_DS;
+  for (int p = 0; p <= TSM_DS; ++p) {
     if (!has_prec(g, p)) continue;
     TSM_TRY(g->links[p].reserve(link_bytes(p, V)));
     count_launches(1);
@@ -162,6 +177,7 @@ int build_links(tsm_gauge* g, const double* links_host) {
       case TSM_F32: pack_links_f32<<<nb, BS>>>(src, g->links[p].as<float4>(), V); break;
       case TSM_F16: pack_links_16<false><<<nb, BS>>>(src, g->links[p].as<uint4>(), V); break;
       case TSM_BF16: pack_links_16<true><<<nb, BS>>>(src, g->links[p].as<uint4>(), V); break;
+      case TSM_DS: pack_links_ds<<<nb, BS>>>(src, g->links[p].as<float4>(), V); break;
     }
     TSM_CUDA(cudaGetLastError());
   }
@@ -179,6 +195,7 @@ int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, in
     case TSM_F32: z4_kernel<TSM_F32><<<grid, BS, 0, s>>>(seed, first, V, out); break;
     case TSM_F16: z4_kernel<TSM_F16><<<grid, BS, 0, s>>>(seed, first, V, out); break;
     case TSM_BF16: z4_kernel<TSM_BF16><<<grid, BS, 0, s>>>(seed, first, V, out); break;
+    case TSM_DS: z4_kernel<TSM_DS><<<grid, BS, 0, s>>>(seed, first, V, out); break;
     default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
   }
   TSM_CUDA(cudaGetLastError());
@@ -227,6 +244,7 @@ int spinor_convert(const tsm_gauge* g, int pd, void* dst, int ps, const void* sr
     case TSM_F32: return convert_from<TSM_F32>(ps, dst, src, V, nrhs, gamma5, s);
     case TSM_F16: return convert_from<TSM_F16>(ps, dst, src, V, nrhs, gamma5, s);
     case TSM_BF16: return convert_from<TSM_BF16>(ps, dst, src, V, nrhs, gamma5, s);
+    case TSM_DS: return convert_from<TSM_DS>(ps, dst, src, V, nrhs, gamma5, s);
   }
   return fail(TSM_ERR_INVALID_ARG, "bad precision %d", pd);
 }

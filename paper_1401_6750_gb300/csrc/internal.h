@@ -97,7 +97,7 @@ struct tsm_gauge {
   tsm_ctx* ctx = nullptr;
   tsm::Geom geom{};
   unsigned precisions = 0;
-  tsm::DevBuf links[4];
+  tsm::DevBuf links[5];  // indexed by precision (TSM_DS: float-float twin of the FP64 copy)
   std::mutex mu;  // guards the caches below
   std::map<long long, std::unique_ptr<tsm::SolverWorkspace, tsm::SolverWsDeleter>> solver_ws;
   std::map<long long, std::unique_ptr<tsm::EoWorkspace, tsm::EoWsDeleter>> eo_ws;

@@ -118,7 +118,7 @@ struct Solver {
     TSM_TRY(w.r.reserve(field_bytes(T::PA, V, nrhs)));
     TSM_TRY(w.p.reserve(field_bytes(T::PS, V, nrhs)));
     TSM_TRY(w.q.reserve(field_bytes(T::PS, V, nrhs)));
-    if (T::XACC) TSM_TRY(w.xacc.reserve(field_bytes(TSM_F64, V, nrhs)));
+    if (T::XACC) TSM_TRY(w.xacc.reserve(field_bytes(T::PXA, V, nrhs)));
     if (w.h_st) cudaFreeHost(w.h_st);
     if (w.h_mask) cudaFreeHost(w.h_mask);
     w.h_st = nullptr;
@@ -260,7 +260,7 @@ struct Solver {
     const void* xsrc = w.x.p;
     count_launches(T::XACC ? 4 : 3);
     if (T::XACC) {
-      k_fold<T::PA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.mask.as<int>(), g->geom.V);
+      k_fold<T::PA, T::PXA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.p, w.mask.as<int>(), g->geom.V);
       xsrc = w.xacc.p;
     }
     {
@@ -300,8 +300,8 @@ struct Solver {
       EpiInitB<Rp, T::PP> e{w.b.p, V, w.st.as<RhsState>(), slots(w), prm};
       launch_dslash<Rp, +1, T::PP, T::PLp>(w.nr_p, args(g, T::PLp, w.t.p, kappa, -mup, nrhs), e, s);
     }
-    k_init<T::PP, T::PA, T::PS, T::XACC>
-        <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.as<double2>(), w.st.as<RhsState>(), g->geom.V);
+    k_init<T::PP, T::PA, T::PS, T::XACC, T::PXA>
+        <<<eg, EW_BS, 0, s>>>(w.b.p, w.r.p, w.x.p, w.p.p, w.xacc.p, w.st.as<RhsState>(), g->geom.V);
     TSM_CUDA(cudaGetLastError());
     const int k = chunk_iterations();
     const long long limit = (long long)max_iter / k + 64;  // host-side bound on chunks
@@ -334,7 +334,7 @@ struct Solver {
     }
     count_launches(1);
     // solution (x_acc + x for the reliable-update solver) in the precise precision, into w.t
-    k_output<T::PA, T::PP, T::XACC><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.as<double2>(), w.t.p, gamma5_out,
+    k_output<T::PA, T::PP, T::XACC, T::PXA><<<eg, EW_BS, 0, s>>>(w.x.p, w.xacc.p, w.t.p, gamma5_out,
                                                           g->geom.V);
     TSM_TRY(spinor_convert(g, out_prec, x_out, T::PP, w.t.p, nrhs, 0, s));
     int bad = 0;

@@ -28,19 +28,28 @@ struct SolveParams {
 
 template <int KIND>
 struct Traits;
+// Rs / Rp: arithmetic of the sloppy / precise operator; PS, PA, PP: storage of
+// p and Ap, of x and r, and of b and the precise operator's fields; PLs, PLp:
+// link copies; PX: input of the precise operator (x, or the accumulated
+// solution when XACC); PXA: storage of that accumulator.
 template <>
 struct Traits<TSM_SOLVER_F64> {
   using Rs = double;
   using Rp = double;
   static constexpr int PS = TSM_F64, PA = TSM_F64, PP = TSM_F64, PLs = TSM_F64, PLp = TSM_F64, PX = TSM_F64;
+  static constexpr int PXA = TSM_F64;
   static constexpr bool XACC = false, SCALED = false;
   static constexpr double DELTA = 0.0;
 };
+// The precise side works in float-float (about 44-bit significands): the true
+// residual it certifies is many decades below rho = 1e-8, and GB300 runs it
+// on the FP32 pipes instead of its narrow FP64 unit.
 template <>
 struct Traits<TSM_SOLVER_F32_RELIABLE> {
   using Rs = float;
-  using Rp = double;
-  static constexpr int PS = TSM_F32, PA = TSM_F32, PP = TSM_F64, PLs = TSM_F32, PLp = TSM_F64, PX = TSM_F64;
+  using Rp = dsf;
+  static constexpr int PS = TSM_F32, PA = TSM_F32, PP = TSM_DS, PLs = TSM_F32, PLp = TSM_DS, PX = TSM_DS;
+  static constexpr int PXA = TSM_DS;
   static constexpr bool XACC = true, SCALED = false;
   // FP32 recurrences stay accurate over three decades below the last true residual
   static constexpr double DELTA = 1e-3;
@@ -50,6 +59,7 @@ struct Traits<TSM_SOLVER_LP_F16> {
   using Rs = float;
   using Rp = float;
   static constexpr int PS = TSM_F16, PA = TSM_F32, PP = TSM_F32, PLs = TSM_F16, PLp = TSM_F32, PX = TSM_F32;
+  static constexpr int PXA = TSM_F32;
   static constexpr bool XACC = false, SCALED = true;
   static constexpr double DELTA = 0.1;
 };
@@ -58,6 +68,7 @@ struct Traits<TSM_SOLVER_LP_BF16> {
   using Rs = float;
   using Rp = float;
   static constexpr int PS = TSM_BF16, PA = TSM_F32, PP = TSM_F32, PLs = TSM_BF16, PLp = TSM_F32, PX = TSM_F32;
+  static constexpr int PXA = TSM_F32;
   static constexpr bool XACC = false, SCALED = true;
   static constexpr double DELTA = 0.1;
 };
@@ -282,8 +293,8 @@ struct EpiResidual {
 };
 
 // ---------------------------------------------------------------- elementwise kernels
-template <int PB, int PA, int PS, bool XACC>
-__global__ void k_init(const void* b, void* r, void* x, void* p, double2* xacc, const RhsState* st, int V) {
+template <int PB, int PA, int PS, bool XACC, int PXA>
+__global__ void k_init(const void* b, void* r, void* x, void* p, void* xacc, const RhsState* st, int V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
   if (i >= V) return;
@@ -293,7 +304,7 @@ __global__ void k_init(const void* b, void* r, void* x, void* p, double2* xacc, 
   for (int k = 0; k < 12; ++k) z[k] = mk<double>(0.0, 0.0);
   SpinorIO<PA>::store(r, (size_t)V, rhs, i, v);
   SpinorIO<PA>::store(x, (size_t)V, rhs, i, z);
-  if (XACC) SpinorIO<TSM_F64>::store(xacc, (size_t)V, rhs, i, z);
+  if (XACC) SpinorIO<PXA>::store(xacc, (size_t)V, rhs, i, z);
   const double c = st[rhs].c_r;
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = c * v[k];
@@ -319,27 +330,27 @@ __global__ void k_pupdate(const void* r, void* p, const RhsState* st, int mode, 
   SpinorIO<PS>::store(p, (size_t)V, rhs, i, pv);
 }
 
-// xacc += x; x = 0 (masked): fold the sloppy solution into the FP64 accumulator.
-template <int PA>
-__global__ void k_fold(void* x, double2* xacc, const int* mask, int V) {
+// xacc += x; x = 0 (masked): fold the sloppy solution into the accumulator.
+template <int PA, int PXA>
+__global__ void k_fold(void* x, void* xacc, const int* mask, int V) {
   const int rhs = blockIdx.y;
   if (!mask[rhs]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
   cplx<double> xv[12], av[12];
   SpinorIO<PA>::load(x, (size_t)V, rhs, i, xv);
-  SpinorIO<TSM_F64>::load(xacc, (size_t)V, rhs, i, av);
+  SpinorIO<PXA>::load(xacc, (size_t)V, rhs, i, av);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     av[k] = av[k] + xv[k];
     xv[k] = mk<double>(0.0, 0.0);
   }
-  SpinorIO<TSM_F64>::store(xacc, (size_t)V, rhs, i, av);
+  SpinorIO<PXA>::store(xacc, (size_t)V, rhs, i, av);
   SpinorIO<PA>::store(x, (size_t)V, rhs, i, xv);
 }
 
-template <int PA, int PO, bool XACC>
-__global__ void k_output(const void* x, const double2* xacc, void* out, int gamma5, int V) {
+template <int PA, int PO, bool XACC, int PXA>
+__global__ void k_output(const void* x, const void* xacc, void* out, int gamma5, int V) {
   const int rhs = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
@@ -347,7 +358,7 @@ __global__ void k_output(const void* x, const double2* xacc, void* out, int gamm
   SpinorIO<PA>::load(x, (size_t)V, rhs, i, v);
   if (XACC) {
     cplx<double> a[12];
-    SpinorIO<TSM_F64>::load(xacc, (size_t)V, rhs, i, a);
+    SpinorIO<PXA>::load(xacc, (size_t)V, rhs, i, a);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = v[k] + a[k];
   }

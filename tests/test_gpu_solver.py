@@ -100,3 +100,27 @@ def test_max_iter_reports_not_converged(ctx):
     for s in stats:
         assert s["converged"] == 0 and s["iterations"] <= 3 and s["true_residual"] > 1e-6
     g.close()
+
+
+@pytest.mark.parametrize("eo", [0, abi.TSM_SOLVER_EO])
+def test_reliable_update_certifies_below_fp32(ctx, eo):
+    """The reliable-update solver's precise operator (float-float, about 44
+    significant bits) certifies residuals far below FP32 resolution: at
+    rho = 1e-10 the oracle's FP64 residual of the returned solution agrees
+    with the reported one to 10% of rho (the float-float rounding, amplified
+    by |x| / |b| of this system, is a few 1e-12)."""
+    from oracle import evenodd
+    dims = (4, 4, 4, 6)
+    kappa, mu, seed, rho = 0.125, 0.01, 1201, 1e-10
+    g, links = gauge(ctx, dims, 0.3, 12, -1, precs=(abi.TSM_F64, abi.TSM_F32))
+    u = lattice.effective_links(links, -1)
+    nat, stats = g.solve_sources(kappa, mu, abi.TSM_SOLVER_F32_RELIABLE | eo, rho, seed, 0, 3)
+    x = g.unpack(nat, abi.TSM_F64, 3).cpu().numpy()
+    for k in range(3):
+        eta = philox.z4_source(dims, seed, k)
+        assert stats[k]["converged"] == 1 and stats[k]["true_residual"] <= rho
+        res = (evenodd.normal_residual(u, eta, x[k], dims, kappa, mu) if eo
+               else _true_residual(u, x[k], eta, kappa, mu))
+        assert res <= 1.1 * rho, (res, stats[k])
+        assert abs(res - stats[k]["true_residual"]) <= 0.1 * rho
+    g.close()
