@@ -16,6 +16,8 @@
 // back and re-read that tile's links from L2 rather than from HBM.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace tsm {
@@ -23,19 +25,24 @@ namespace tsm {
 constexpr int DSLASH_BS = 128;
 
 // Resident blocks per SM the register allocation must allow (__launch_bounds__),
-// per field precision: FP32 measured fastest at 6 (<= 80 registers), 16-bit
-// fields at 6 (<= 80 registers); FP64 and float-float keep the compiler's
-// choice.  TSM_DSLASH_MINB32 / TSM_DSLASH_MINB16 override (variant builds).
+// per field precision, as measured at 24^3 x 48: FP32 and 16-bit fields 6
+// (<= 80 registers), float-float 3 (<= 168); FP64 keeps the compiler's choice.
+// TSM_DSLASH_MINB32 / _MINB16 / _MINBDS override them (variant builds).
 #ifndef TSM_DSLASH_MINB32
 #define TSM_DSLASH_MINB32 6
 #endif
 #ifndef TSM_DSLASH_MINB16
 #define TSM_DSLASH_MINB16 6
 #endif
+#ifndef TSM_DSLASH_MINBDS
+#define TSM_DSLASH_MINBDS 3
+#endif
 template <int PIN>
 struct MinBlocks {
   static constexpr int value =
-      (PIN == TSM_F32) ? TSM_DSLASH_MINB32 : ((PIN == TSM_F16 || PIN == TSM_BF16) ? TSM_DSLASH_MINB16 : 1);
+      (PIN == TSM_F32) ? TSM_DSLASH_MINB32
+                       : ((PIN == TSM_F16 || PIN == TSM_BF16) ? TSM_DSLASH_MINB16
+                                                               : (PIN == TSM_DS ? TSM_DSLASH_MINBDS : 1));
 };
 
 struct DslashArgs {
@@ -316,6 +323,93 @@ __device__ __forceinline__ void stencil_dir(cplx<R> (&acc)[NR][12], const Dslash
   }
 }
 
+// f z for a unit factor f = sgn * (rot ? i : 1) (exact in every real type)
+template <typename R>
+__device__ __forceinline__ cplx<R> unit_times(cplx<R> z, bool rot, bool neg) {
+  cplx<R> t = rot ? mk<R>(-z.im, z.re) : z;
+  return neg ? mk<R>(-t.re, -t.im) : t;
+}
+
+// All eight hops of one site in a loop with the direction as a runtime value:
+// one body instead of eight unrolled ones.  Used for float-float sums, whose
+// unrolled form is too large for the instruction cache.  Same arithmetic as
+// stencil_dir: h0 = p0 + f0 p_j0, h1 = p1 + f1 p_j1 (see project_pair),
+// w = U h (U^dag on backward hops), lower spins = g0 w_k0, g1 w_k1.
+template <int SF, typename R, int PIN, int PL, int NR, bool EO>
+__device__ __forceinline__ void stencil_rolled(cplx<R> (&acc)[NR][12], const DslashArgs& a, int r0,
+                                               const bool (&act)[NR], int i, const int c[4]) {
+  const size_t V = (size_t)a.g.V;
+  const size_t FS = EO ? V / 2 : V;
+#pragma unroll 1
+  for (int hop = 0; hop < 8; ++hop) {
+    const int mu = hop >> 1;
+    const bool back = (hop & 1) != 0;
+    const int S = back ? -SF : SF;  // projector sign of this hop
+    const int stride = dir_stride(a.g, mu);
+    const int n = back ? bwd_site(a.g, i, c, mu, stride) : fwd_site(a.g, i, c, mu, stride);
+    cplx<R> u[3][3];
+    LinkIO<PL>::load(a.links, V, mu, back ? n : i, u);
+    if (back) {  // U^dag in place
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        u[x][x] = conjc(u[x][x]);
+#pragma unroll
+        for (int y = x + 1; y < 3; ++y) {
+          const cplx<R> t = u[x][y];
+          u[x][y] = conjc(u[y][x]);
+          u[y][x] = conjc(t);
+        }
+      }
+    }
+    const bool edge = (mu == 3) && (back ? (c[3] == 0) : (c[3] == a.g.L[3] - 1));
+    const bool flip = edge && a.g.bc < 0;
+    // projection h0 = p0 + f0 p_j0, h1 = p1 + f1 p_j1
+    const int j0 = (mu == 0 || mu == 1) ? 3 : 2, j1 = 5 - j0;
+    const bool rot = (mu == 0 || mu == 2);
+    const bool neg0 = (mu == 3) ? (S < 0) : (S > 0);
+    const bool neg1 = (mu == 0) ? (S > 0) : (S < 0);
+    // lower spins: acc6 += g0 w_k0, acc9 += g1 w_k1
+    const int k0 = (mu == 0 || mu == 1) ? 1 : 0;
+    const bool gneg0 = (S < 0);
+    const bool gneg1 = (mu == 1 || mu == 2) ? (S > 0) : (S < 0);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      if (!act[q]) continue;
+      cplx<R> p[12];
+      SpinorIO<PIN>::load(a.in, FS, r0 + q, EO ? (n >> 1) : n, p);
+      cplx<R> h0[3], h1[3];
+#pragma unroll
+      for (int col = 0; col < 3; ++col) {
+        h0[col] = p[col] + unit_times(p[3 * j0 + col], rot, neg0);
+        h1[col] = p[3 + col] + unit_times(p[3 * j1 + col], rot, neg1);
+      }
+      cplx<R> w0[3], w1[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        w0[x] = mk<R>(0, 0);
+        w1[x] = mk<R>(0, 0);
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          cmac(w0[x], u[x][y], h0[y]);
+          cmac(w1[x], u[x][y], h1[y]);
+        }
+        if (flip) {
+          w0[x] = mk<R>(-w0[x].re, -w0[x].im);
+          w1[x] = mk<R>(-w1[x].re, -w1[x].im);
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        acc[q][x] = acc[q][x] + w0[x];
+        acc[q][3 + x] = acc[q][3 + x] + w1[x];
+        const cplx<R> a0 = k0 ? w1[x] : w0[x], a1 = k0 ? w0[x] : w1[x];
+        acc[q][6 + x] = acc[q][6 + x] + unit_times(a0, rot, gneg0);
+        acc[q][9 + x] = acc[q][9 + x] + unit_times(a1, rot, gneg1);
+      }
+    }
+  }
+}
+
 // Full operator at site i for NR right-hand sides: out = in + i tw g5 in - kappa * hop.
 template <int SF, typename R, int PIN, int PL, int NR>
 __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0, const bool (&act)[NR],
@@ -326,10 +420,14 @@ __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashA
   for (int j = 0; j < NR; ++j)
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[j][k] = mk<R>(0, 0);
-  stencil_dir<0, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
-  stencil_dir<1, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
-  stencil_dir<2, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
-  stencil_dir<3, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  if constexpr (std::is_same<R, dsf>::value) {
+    stencil_rolled<SF, R, PIN, PL, NR, false>(out, a, r0, act, i, c);
+  } else {
+    stencil_dir<0, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+    stencil_dir<1, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+    stencil_dir<2, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+    stencil_dir<3, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  }
   const R kap = arg_kappa<R>(a), tw = arg_tw<R>(a);
 #pragma unroll
   for (int j = 0; j < NR; ++j) {
@@ -439,10 +537,14 @@ __device__ __forceinline__ void apply_site_eo(cplx<R> (&out)[NR][12], const Dsla
   for (int q = 0; q < NR; ++q)
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[q][k] = mk<R>(0, 0);
-  stencil_dir<0, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
-  stencil_dir<1, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
-  stencil_dir<2, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
-  stencil_dir<3, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  if constexpr (std::is_same<R, dsf>::value) {
+    stencil_rolled<SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  } else {
+    stencil_dir<0, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+    stencil_dir<1, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+    stencil_dir<2, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+    stencil_dir<3, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  }
   R c0, c1, h0, h1;
   EoCoef<R>::get(a, c0, c1, h0, h1);
   const size_t FS = (size_t)a.g.V / 2;
