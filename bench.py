@@ -220,6 +220,22 @@ def _dslash_roofline(g, abi, torch, peak, prec, nrhs, reps=10):
             "bytes_per_launch": bytes_, "us_per_launch": t * 1e6, "l2": "flushed (512 MB write) before each launch"}
 
 
+def measured_traffic(kernel_class):
+    """DRAM bytes per launch of `kernel_class` from the committed ncu capture
+    (profiles/roofline_traffic.txt), or None when that capture was taken on
+    different CUDA sources or for another kernel."""
+    from paper_1401_6750_gb300 import build
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "roofline_traffic.txt")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_class") != kernel_class or rec.get("source_digest") != build.source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def probe(args):
     """Small, self-contained workloads for profiler captures (no timing output)."""
     import ctypes
@@ -450,7 +466,7 @@ def main():
     dom = kern[0]
     achieved = dom["bytes"] / dom["seconds"] / 1e9
     roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": measured_traffic(dom["name"]),
                 "us_per_launch": dom["seconds"] / dom["launches"] * 1e6,
                 "bytes_per_launch": dom["bytes"] / dom["launches"],
                 "share_of_step": dom["seconds"] / total_s}

@@ -234,12 +234,13 @@ int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec,
  * memory pool or allocator that forbids new device allocations, or latency-
  * sensitive loops where an allocation would synchronise the device.  The
  * caller still passes the solutions and the output; the library's own
- * scratch (g5 A s for every source, the per-plane partial projections and a
- * copy of the momentum list) lives in a fixed array of
- * TSM_CONTRACT_NOALLOC_MAX_BYTES compiled into the library, which every GPU
- * that loads the library holds until the process exits.  Needs
+ * scratch (g5 A s for every source, the 160 site fields, the per-plane
+ * partial projections and a copy of the momentum list) lives in a fixed
+ * array of TSM_CONTRACT_NOALLOC_MAX_BYTES compiled into the library, which
+ * every GPU that loads the library holds until the process exits.  Needs
  *   256-rounded(12 n_mom) + 256-rounded(nsrc * V * 16 * NCH)
- *   + 256-rounded(Lz * T * 160 * (2R+1)^2 * 16)  bytes  (R = max |n_i|)
+ *   + 256-rounded(160 * V * c) + 256-rounded(Lz * T * 160 * (2R+1)^2 * 16)
+ *   bytes (R = max |n_i|; c = 8 for F32 solutions, 16 for F64)
  * and returns TSM_ERR_INVALID_ARG, touching nothing, when that exceeds the
  * maximum.  The first call on a device looks up the array's device address
  * and uploads a constant table there (make it before any stream capture);

@@ -50,6 +50,18 @@ def _digest(extra_flags):
     return h.hexdigest()
 
 
+def source_digest():
+    """sha256 of the CUDA sources and public headers (names and contents): a
+    profile taken on one tree is valid for another only if this matches."""
+    h = hashlib.sha256()
+    files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def build(verbose=False, force=False, extra_flags=None, jobs=None):
     # TSM_NVCC_FLAGS adds compile definitions (variant builds for measurements)
     if extra_flags is None:

@@ -188,10 +188,21 @@ struct SolverEO {
     return args(g, pl, in, ctr, 1, kappa, 1.0, tau, kappa, 0.0, nrhs);
   }
 
+  static double delta() {
+    // TSM_RU_DELTA_<kind> overrides the residual-replacement threshold (measurement only)
+    static const double d = [] {
+      char name[32];
+      snprintf(name, sizeof(name), "TSM_RU_DELTA_%d", KIND);
+      const char* e = getenv(name);
+      return e ? atof(e) : T::DELTA;
+    }();
+    return d;
+  }
+
   static SolveParams params(const tsm_gauge* g, double rho, int max_iter) {
     SolveParams p;
     p.rho2 = rho * rho;
-    p.delta2 = T::DELTA * T::DELTA;
+    p.delta2 = delta() * delta();
     p.inv_ncomp = 1.0 / (12.0 * (double)(g->geom.V / 2));
     p.max_iter = max_iter;
     p.scaled = T::SCALED ? 1 : 0;
