@@ -70,7 +70,13 @@ enum tsm_op {
   TSM_OP_M = 0,     /* M(mu)                                  */
   TSM_OP_MDAG = 1,  /* M(mu)^dag                              */
   TSM_OP_A = 2,     /* Wilson part A = M(mu = 0)              */
-  TSM_OP_MDAGM = 3  /* M^dag M                                */
+  TSM_OP_MDAGM = 3, /* M^dag M                                */
+  /* Even-odd Schur operator Mhat = M_oo - M_oe M_ee^{-1} M_eo and its adjoint
+   * (see TSM_SOLVER_EO): they act on the odd sites of the input and write the
+   * result on the odd sites, zeros on the even sites.  Need every extent
+   * even. */
+  TSM_OP_MHAT = 4,
+  TSM_OP_MHATDAG = 5
 };
 
 /* Solvers for Eq. 1 (all CG on M^dag M, x0 = 0, see tsm_solve_sources). */
@@ -84,7 +90,7 @@ enum tsm_solver {
   /* Flag OR-ed into any of the above: solve the even-odd (Schur complement)
    * system Mhat s_o = eta_o - M_oe M_ee^{-1} eta_e by CG on Mhat^dag Mhat on the
    * odd sites, then reconstruct s_e = M_ee^{-1}(eta_e - M_eo s_o).  Same
-   * solutions and output layout; needs an even L[0].  `rho` then bounds the
+   * solutions and output layout; needs every extent even.  `rho` then bounds the
    * residual of the preconditioned normal equations, and the stats report
    * it.  Not available in tsm_solve_batch. */
   TSM_SOLVER_EO = 16
@@ -152,11 +158,11 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src,
 /* Solve M s_r = eta_r (Eq. 1) for the Z4 sources r = first_src ..
  * first_src + nsrc - 1 by CG on M^dag M with x0 = 0, stopping when the
  * iterated residual of the normal equations drops below rho and the true
- * residual (recomputed with the precise operator: FP64 for F64 and
- * F32_RELIABLE, FP32 for the LP solvers) confirms it; otherwise the
+ * residual (recomputed with the precise operator: FP64 for F64,
+ * float-float for F32_RELIABLE, FP32 for the LP solvers) confirms it; otherwise the
  * iteration restarts from the true residual, up to max_iter in total.
  * Solutions are written in native layout: F64 for TSM_SOLVER_F64 and
- * TSM_SOLVER_F32_RELIABLE (its FP64 accumulated solution), F32 for the LP
+ * TSM_SOLVER_F32_RELIABLE (its float-float accumulated solution), F32 for the LP
  * solvers.  stats_host (optional) receives nsrc records.  Returns
  * TSM_ERR_NOT_CONVERGED if any source missed rho (outputs still written).
  * Right-hand sides are batched `nrhs_per_launch` at a time (<= 0: all). */

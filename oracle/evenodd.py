@@ -23,7 +23,10 @@ from . import dirac, lattice, solver
 
 
 def parity(dims):
-    """(t, z, y, x) integer array: 0 on even sites, 1 on odd sites."""
+    """(t, z, y, x) integer array: 0 on even sites, 1 on odd sites.  The split
+    is a checkerboard of the hopping term only when every extent is even."""
+    if any(n % 2 for n in dims):
+        raise ValueError("the even-odd form needs even extents, got %s" % (dims,))
     x, y, z, t = lattice.coords(dims)
     return (x + y + z + t) & 1
 

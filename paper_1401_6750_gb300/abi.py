@@ -15,7 +15,7 @@ c_int, c_double, c_uint64, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_double, 
 TSM_OK, TSM_ERR_INVALID_ARG, TSM_ERR_CUDA, TSM_ERR_OOM = 0, 1, 2, 3
 TSM_ERR_NOT_CONVERGED, TSM_ERR_NONFINITE, TSM_ERR_UNIMPLEMENTED = 4, 5, 6
 TSM_F64, TSM_F32, TSM_F16, TSM_BF16 = 0, 1, 2, 3
-TSM_OP_M, TSM_OP_MDAG, TSM_OP_A, TSM_OP_MDAGM = 0, 1, 2, 3
+TSM_OP_M, TSM_OP_MDAG, TSM_OP_A, TSM_OP_MDAGM, TSM_OP_MHAT, TSM_OP_MHATDAG = 0, 1, 2, 3, 4, 5
 TSM_SOLVER_F64, TSM_SOLVER_F32_RELIABLE, TSM_SOLVER_LP_F16, TSM_SOLVER_LP_BF16 = 0, 1, 2, 3
 TSM_SOLVER_EO = 16  # flag: even-odd preconditioned CG (OR with a solver)
 TSM_N_INSERTIONS = 160

@@ -126,14 +126,15 @@ __global__ void multi_init(const InstDesc* __restrict__ d, int n) {
   const int lb = blockIdx.x - I.eblock0, rhs = lb / I.eblk, i = (lb % I.eblk) * EW_BS + threadIdx.x;
   if (i >= I.g.V) return;
   const size_t V = (size_t)I.g.V;
-  cplx<double> v[12], z[12];
+  using R = ew_real<T::PP, T::PA, T::PS, (T::XACC ? T::PXA : T::PA)>;
+  cplx<R> v[12], z[12];
   SpinorIO<T::PP>::load(I.b, V, rhs, i, v);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) z[k] = mk<double>(0.0, 0.0);
+  for (int k = 0; k < 12; ++k) z[k] = mk<R>(0, 0);
   SpinorIO<T::PA>::store(I.r, V, rhs, i, v);
   SpinorIO<T::PA>::store(I.x, V, rhs, i, z);
   if (T::XACC) SpinorIO<T::PXA>::store(I.xacc, V, rhs, i, z);
-  const double c = I.st[rhs].c_r;
+  const R c = (R)I.st[rhs].c_r;
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = c * v[k];
   SpinorIO<T::PS>::store(I.p, V, rhs, i, v);
@@ -164,13 +165,14 @@ __global__ void multi_fold(const InstDesc* __restrict__ d, int n) {
   const int lb = blockIdx.x - I.eblock0, rhs = lb / I.eblk, i = (lb % I.eblk) * EW_BS + threadIdx.x;
   if (!I.mask[rhs] || i >= I.g.V) return;
   const size_t V = (size_t)I.g.V;
-  cplx<double> xv[12], av[12];
+  using R = ew_real<T::PA, T::PXA>;
+  cplx<R> xv[12], av[12];
   SpinorIO<T::PA>::load(I.x, V, rhs, i, xv);
   SpinorIO<T::PXA>::load(I.xacc, V, rhs, i, av);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     av[k] = av[k] + xv[k];
-    xv[k] = mk<double>(0.0, 0.0);
+    xv[k] = mk<R>(0, 0);
   }
   SpinorIO<T::PXA>::store(I.xacc, V, rhs, i, av);
   SpinorIO<T::PA>::store(I.x, V, rhs, i, xv);
@@ -182,10 +184,11 @@ __global__ void multi_output(const InstDesc* __restrict__ d, int n) {  // t = x 
   const int lb = blockIdx.x - I.eblock0, rhs = lb / I.eblk, i = (lb % I.eblk) * EW_BS + threadIdx.x;
   if (i >= I.g.V) return;
   const size_t V = (size_t)I.g.V;
-  cplx<double> v[12];
+  using R = ew_real<T::PA, T::PP, (T::XACC ? T::PXA : T::PA)>;
+  cplx<R> v[12];
   SpinorIO<T::PA>::load(I.x, V, rhs, i, v);
   if (T::XACC) {
-    cplx<double> a[12];
+    cplx<R> a[12];
     SpinorIO<T::PXA>::load(I.xacc, V, rhs, i, a);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = v[k] + a[k];

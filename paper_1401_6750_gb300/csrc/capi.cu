@@ -215,7 +215,7 @@ int tsm_spinor_unpack(const tsm_gauge* g, int prec, const void* native_dev, doub
 
 int tsm_dslash_tm(tsm_gauge* g, double kappa, double mu, int op, int prec, const void* in_dev, void* out_dev,
                   int nrhs, void* stream) {
-  if (!g || !in_dev || !out_dev || !valid_prec(prec) || nrhs < 0 || op < TSM_OP_M || op > TSM_OP_MDAGM)
+  if (!g || !in_dev || !out_dev || !valid_prec(prec) || nrhs < 0 || op < TSM_OP_M || op > TSM_OP_MHATDAG)
     return fail(TSM_ERR_INVALID_ARG, "tsm_dslash_tm: bad argument");
   if (!isfinite(kappa) || !isfinite(mu)) return fail(TSM_ERR_INVALID_ARG, "kappa and mu must be finite");
   if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
@@ -223,6 +223,8 @@ int tsm_dslash_tm(tsm_gauge* g, double kappa, double mu, int op, int prec, const
   if (nrhs == 0) return TSM_OK;
   if (nrhs > 65535) return fail(TSM_ERR_INVALID_ARG, "nrhs %d > 65535", nrhs);
   TSM_TRY(bind(g));
+  if (op == TSM_OP_MHAT || op == TSM_OP_MHATDAG)
+    return schur_apply(g, prec, op == TSM_OP_MHATDAG, kappa, mu, in_dev, out_dev, nrhs, pick_stream(g, stream));
   return dslash_apply(g, prec, op, kappa, mu, in_dev, out_dev, nrhs, pick_stream(g, stream));
 }
 
@@ -238,7 +240,8 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src, int 
 static int check_solver_args(const tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter) {
   if (!g) return fail(TSM_ERR_INVALID_ARG, "gauge is NULL");
   if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver %d", solver);
-  if ((solver & TSM_SOLVER_EO) && g->geom.L[0] % 2) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need an even L[0]");
+  if ((solver & TSM_SOLVER_EO) && !eo_lattice(g->geom))
+    return fail(TSM_ERR_INVALID_ARG, "even-odd solves need even extents in all four directions");
   if (!(rho > 0.0) || !(rho < 1.0)) return fail(TSM_ERR_INVALID_ARG, "rho must lie in (0, 1), got %g", rho);
   if (max_iter < 1) return fail(TSM_ERR_INVALID_ARG, "max_iter must be >= 1");
   if (!isfinite(kappa) || !isfinite(mu) || kappa <= 0.0) return fail(TSM_ERR_INVALID_ARG, "bad kappa or mu");

@@ -9,6 +9,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tsm.h"
 
 namespace tsm {
@@ -67,6 +69,17 @@ __device__ __forceinline__ dsf normalise(dsf a) {
   const float bb = s - a.hi;
   return dsf(s, (a.hi - (s - bb)) + (a.lo - bb));
 }
+
+// Arithmetic of element-wise kernels over fields of precisions P...: double
+// when any of them carries more than a float (FP64, float-float), float
+// otherwise (GB300's FP64 pipe, conversions included, is 1/64 of FP32).
+template <int... P>
+struct EwReal {
+  static constexpr bool wide = ((P == TSM_F64 || P == TSM_DS) || ...);
+  using type = typename std::conditional<wide, double, float>::type;
+};
+template <int... P>
+using ew_real = typename EwReal<P...>::type;
 
 // ---------------------------------------------------------------- complex
 template <typename R>

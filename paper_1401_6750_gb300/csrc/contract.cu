@@ -265,6 +265,7 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
         cplx<R> acc[XY_NC];
 #pragma unroll
         for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+#pragma unroll 6
         for (int x = 0; x < lx; ++x) {
           const cplx<R> v = src[x];
           const cplx<R>* tw = twx + (size_t)x * nx + n0;
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
         cplx<R> acc[XY_NC];
 #pragma unroll
         for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+#pragma unroll 6
         for (int row = 0; row < ly; ++row) {
           const cplx<R> v = src[(size_t)row * nx];
           const cplx<R>* tw = twy + (size_t)row * nx + n0;

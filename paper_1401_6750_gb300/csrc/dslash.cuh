@@ -518,8 +518,8 @@ __global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_kerne
 }
 
 // ---------------------------------------------------------------- even-odd operator
-// Full site of checkerboard index j on parity p (Lx even: sites 2j and 2j+1
-// share y, z, t and have opposite parity).
+// Full site of checkerboard index j on parity p (all extents even: sites 2j
+// and 2j+1 share y, z, t and have opposite parity).
 __device__ __forceinline__ int eo_site(const Geom& g, int j, int p, int c[4]) {
   const int i0 = 2 * j;
   site_coords(g, i0, c);

@@ -1,4 +1,5 @@
-// Even-odd (Schur complement) preconditioned solves of Eq. 1.
+// Even-odd (Schur complement) preconditioned solves of Eq. 1 (every lattice
+// extent even, so that every hop joins sites of opposite parity).
 //
 // With sites split by parity, M = [[M_ee, M_eo], [M_oe, M_oo]] where
 // M_ee = M_oo = 1 + i mu' g5 is site-local and M_eo = -kappa H_eo is the
@@ -38,7 +39,7 @@ __global__ void k_gather_eo(const void* full, void* even, void* odd, Geom g) {
   int c[4];
   site_coords(g, i, c);
   const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-  cplx<double> v[12];
+  cplx<ew_real<P>> v[12];
   SpinorIO<P>::load(full, (size_t)g.V, rhs, i, v);
   SpinorIO<P>::store(par ? odd : even, (size_t)g.V / 2, rhs, i >> 1, v);
 }
@@ -52,11 +53,12 @@ __global__ void k_scatter_eo(void* full, const void* even, const void* odd, Geom
   int c[4];
   site_coords(g, i, c);
   const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-  cplx<double> v[12];
+  using R = ew_real<PO, PI>;
+  cplx<R> v[12];
   SpinorIO<PI>::load(par ? odd : even, (size_t)g.V / 2, rhs, i >> 1, v);
   if (gamma5) {
 #pragma unroll
-    for (int k = 6; k < 12; ++k) v[k] = mk<double>(-v[k].re, -v[k].im);
+    for (int k = 6; k < 12; ++k) v[k] = mk<R>(-v[k].re, -v[k].im);
   }
   SpinorIO<PO>::store(full, (size_t)g.V, rhs, i, v);
 }
@@ -67,13 +69,12 @@ __global__ void k_diag(void* out, const void* in, double cr, double ci, int vh) 
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
   if (j >= vh) return;
-  cplx<double> v[12];
+  using R = ew_real<P>;
+  cplx<R> v[12];
   SpinorIO<P>::load(in, (size_t)vh, rhs, j, v);
+  const R a = (R)cr, b = (R)ci;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const double g5 = k < 6 ? 1.0 : -1.0;
-    v[k] = cr * v[k] + (g5 * ci) * times_i(v[k]);
-  }
+  for (int k = 0; k < 12; ++k) v[k] = a * v[k] + (k < 6 ? b : -b) * times_i(v[k]);
   SpinorIO<P>::store(out, (size_t)vh, rhs, j, v);
 }
 
@@ -464,10 +465,74 @@ int solve_eo_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_ite
 
 }  // namespace
 
+namespace {
+
+DslashArgs eo_args(const tsm_gauge* g, int prec, const void* in, const void* ctr, int par, double kappa, double c0,
+                   double c1, double h0, double h1, int nrhs) {
+  DslashArgs a;
+  a.g = g->geom;
+  a.links = g->links[prec].p;
+  a.in = in;
+  a.nrhs = nrhs;
+  a.nblk = (g->geom.V / 2 + DSLASH_BS - 1) / DSLASH_BS;
+  set_coeffs(a, kappa, 0.0);
+  set_eo(a, ctr, par, c0, c1, h0, h1);
+  return a;
+}
+
+// out_o = Mhat in_o (dag: Mhat^dag) on half-volume fields; t_e is scratch
+template <typename R, int P, int SF>
+void mhat_launch(const tsm_gauge* g, double kappa, double tau, const void* in_o, void* t_e, void* out_o, int nrhs,
+                 cudaStream_t s) {
+  const size_t Vh = (size_t)g->geom.V / 2;
+  const double d = 1.0 + tau * tau;
+  EpiStore<R, P> et{t_e, Vh, 0, RedSlots{nullptr, nullptr}};
+  EpiStore<R, P> eo{out_o, Vh, 0, RedSlots{nullptr, nullptr}};
+  launch_dslash_eo<R, SF, P, P>(1, eo_args(g, P, in_o, nullptr, 0, kappa, 0.0, 0.0, -kappa / d, kappa * tau / d, nrhs),
+                                et, s);
+  launch_dslash_eo<R, SF, P, P>(1, eo_args(g, P, t_e, in_o, 1, kappa, 1.0, tau, kappa, 0.0, nrhs), eo, s);
+}
+
+template <typename R, int P>
+int mhat_apply(tsm_gauge* g, int dag, double kappa, double mu, const void* in, void* out, int nrhs, cudaStream_t s) {
+  const int V = g->geom.V;
+  const size_t half = (size_t)nrhs * spinor_chunks(P) * (size_t)(V / 2) * 16;
+  std::lock_guard<std::mutex> lock(g->mu);
+  TSM_TRY(g->eo_tmp.reserve(3 * half));
+  char* base = g->eo_tmp.as<char>();
+  void *in_o = base, *t_e = base + half, *out_o = base + 2 * half;
+  const double mup = 2.0 * kappa * mu;
+  dim3 fg((V + EW_BS - 1) / EW_BS, nrhs);
+  count_launches(5);
+  k_gather_eo<P><<<fg, EW_BS, 0, s>>>(in, t_e, in_o, g->geom);  // the even half lands in scratch
+  if (dag)
+    mhat_launch<R, P, +1>(g, kappa, -mup, in_o, t_e, out_o, nrhs, s);
+  else
+    mhat_launch<R, P, -1>(g, kappa, mup, in_o, t_e, out_o, nrhs, s);
+  TSM_CUDA(cudaMemsetAsync(t_e, 0, half, s));  // zeros on the even sites of the result
+  k_scatter_eo<P, P><<<fg, EW_BS, 0, s>>>(out, t_e, out_o, g->geom, 0);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+}  // namespace
+
+int schur_apply(tsm_gauge* g, int prec, int dag, double kappa, double mu, const void* in, void* out, int nrhs,
+                cudaStream_t s) {
+  if (!eo_lattice(g->geom)) return fail(TSM_ERR_INVALID_ARG, "the Schur operator needs even extents");
+  switch (prec) {
+    case TSM_F64: return mhat_apply<double, TSM_F64>(g, dag, kappa, mu, in, out, nrhs, s);
+    case TSM_F32: return mhat_apply<float, TSM_F32>(g, dag, kappa, mu, in, out, nrhs, s);
+    case TSM_F16: return mhat_apply<float, TSM_F16>(g, dag, kappa, mu, in, out, nrhs, s);
+    case TSM_BF16: return mhat_apply<float, TSM_BF16>(g, dag, kappa, mu, in, out, nrhs, s);
+  }
+  return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+}
+
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                    const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
                    int gamma5_io, tsm_solve_stats* stats, cudaStream_t s) {
-  if (g->geom.L[0] % 2) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need an even Lx");
+  if (!eo_lattice(g->geom)) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need even extents");
   switch (solver & ~TSM_SOLVER_EO) {
     case TSM_SOLVER_F64:
       return solve_eo_kind<TSM_SOLVER_F64>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec,

@@ -91,12 +91,13 @@ __global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out) {
   uint64_t x[4] = {(uint64_t)i, 0ull, 0ull, 0ull};
   philox4x64_10(x, seed, first + (uint64_t)r);
   const uint64_t w = x[0];
-  cplx<double> v[12];
+  using R = ew_real<P>;
+  cplx<R> v[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int z = (int)((w >> (2 * k)) & 3ull);
     // i^z: 0 -> 1, 1 -> i, 2 -> -1, 3 -> -i
-    v[k] = mk<double>(z == 0 ? 1.0 : (z == 2 ? -1.0 : 0.0), z == 1 ? 1.0 : (z == 3 ? -1.0 : 0.0));
+    v[k] = mk<R>((R)(z == 0 ? 1 : (z == 2 ? -1 : 0)), (R)(z == 1 ? 1 : (z == 3 ? -1 : 0)));
   }
   SpinorIO<P>::store(out, (size_t)V, r, i, v);
 }
@@ -131,11 +132,12 @@ __global__ void convert_kernel(void* dst, const void* src, int V, int gamma5) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (i >= V) return;
-  cplx<double> v[12];
+  using R = ew_real<PD, PS>;
+  cplx<R> v[12];
   SpinorIO<PS>::load(src, (size_t)V, r, i, v);
   if (gamma5) {
 #pragma unroll
-    for (int k = 6; k < 12; ++k) v[k] = mk<double>(-v[k].re, -v[k].im);
+    for (int k = 6; k < 12; ++k) v[k] = mk<R>(-v[k].re, -v[k].im);
   }
   SpinorIO<PD>::store(dst, (size_t)V, r, i, v);
 }

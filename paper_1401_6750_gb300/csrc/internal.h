@@ -103,6 +103,7 @@ struct tsm_gauge {
   std::map<long long, std::unique_ptr<tsm::EoWorkspace, tsm::EoWsDeleter>> eo_ws;
   std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws;
   tsm::DevBuf tmp;  // operator scratch (M^dag M intermediate, conversions)
+  tsm::DevBuf eo_tmp;  // Schur operator scratch (three half-volume fields; guarded by mu)
   std::mutex tsm_mu;       // guards the TSM buffers
   tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
   tsm::DevBuf tsm_sol;     // solutions of one batch
@@ -157,6 +158,13 @@ int solver_precise_prec(int solver);
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                    const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
                    int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
+// out = Mhat in (dag: Mhat^dag) on the odd sites of full-layout fields, zero on
+// the even sites (eo.cu)
+int schur_apply(tsm_gauge* g, int prec, int dag, double kappa, double mu, const void* in, void* out, int nrhs,
+                cudaStream_t s);
+// even-odd forms need every extent even: then every hop joins sites of
+// opposite parity (x + y + z + t), and site i has checkerboard index i >> 1
+inline bool eo_lattice(const Geom& g) { return !(g.L[0] % 2 || g.L[1] % 2 || g.L[2] % 2 || g.L[3] % 2); }
 // solver kind without flags; -1 if unknown
 inline int solver_kind(int solver) {
   const int k = solver & ~TSM_SOLVER_EO;

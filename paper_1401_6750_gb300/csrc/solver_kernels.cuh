@@ -300,14 +300,15 @@ __global__ void k_init(const void* b, void* r, void* x, void* p, void* xacc, con
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
   if (i >= V) return;
-  cplx<double> v[12], z[12];
+  using R = ew_real<PB, PA, PS, (XACC ? PXA : PA)>;
+  cplx<R> v[12], z[12];
   SpinorIO<PB>::load(b, (size_t)V, rhs, i, v);
 #pragma unroll
-  for (int k = 0; k < 12; ++k) z[k] = mk<double>(0.0, 0.0);
+  for (int k = 0; k < 12; ++k) z[k] = mk<R>(0, 0);
   SpinorIO<PA>::store(r, (size_t)V, rhs, i, v);
   SpinorIO<PA>::store(x, (size_t)V, rhs, i, z);
   if (XACC) SpinorIO<PXA>::store(xacc, (size_t)V, rhs, i, z);
-  const double c = st[rhs].c_r;
+  const R c = (R)st[rhs].c_r;
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = c * v[k];
   SpinorIO<PS>::store(p, (size_t)V, rhs, i, v);
@@ -339,13 +340,14 @@ __global__ void k_fold(void* x, void* xacc, const int* mask, int V) {
   if (!mask[rhs]) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
-  cplx<double> xv[12], av[12];
+  using R = ew_real<PA, PXA>;
+  cplx<R> xv[12], av[12];
   SpinorIO<PA>::load(x, (size_t)V, rhs, i, xv);
   SpinorIO<PXA>::load(xacc, (size_t)V, rhs, i, av);
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     av[k] = av[k] + xv[k];
-    xv[k] = mk<double>(0.0, 0.0);
+    xv[k] = mk<R>(0, 0);
   }
   SpinorIO<PXA>::store(xacc, (size_t)V, rhs, i, av);
   SpinorIO<PA>::store(x, (size_t)V, rhs, i, xv);
@@ -356,17 +358,18 @@ __global__ void k_output(const void* x, const void* xacc, void* out, int gamma5,
   const int rhs = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= V) return;
-  cplx<double> v[12];
+  using R = ew_real<PA, PO, (XACC ? PXA : PA)>;
+  cplx<R> v[12];
   SpinorIO<PA>::load(x, (size_t)V, rhs, i, v);
   if (XACC) {
-    cplx<double> a[12];
+    cplx<R> a[12];
     SpinorIO<PXA>::load(xacc, (size_t)V, rhs, i, a);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = v[k] + a[k];
   }
   if (gamma5) {
 #pragma unroll
-    for (int k = 6; k < 12; ++k) v[k] = mk<double>(-v[k].re, -v[k].im);
+    for (int k = 6; k < 12; ++k) v[k] = mk<R>(-v[k].re, -v[k].im);
   }
   SpinorIO<PO>::store(out, (size_t)V, rhs, i, v);
 }

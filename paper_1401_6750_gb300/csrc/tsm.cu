@@ -81,7 +81,8 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
   if (p->n_mom < 1 || !p->mom) return fail(TSM_ERR_INVALID_ARG, "need at least one momentum");
   for (int solver : {p->lp_solver, p->hp_solver}) {
     if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver");
-    if ((solver & TSM_SOLVER_EO) && g->geom.L[0] % 2) return fail(TSM_ERR_INVALID_ARG, "even-odd needs an even L[0]");
+    if ((solver & TSM_SOLVER_EO) && !eo_lattice(g->geom))
+      return fail(TSM_ERR_INVALID_ARG, "even-odd needs even extents in all four directions");
     const unsigned need = solver_link_precs(solver);
     if ((g->precisions & need) != need)
       return fail(TSM_ERR_INVALID_ARG, "solver %d needs gauge copies 0x%x", solver, need);

@@ -101,3 +101,36 @@ def test_rejects_non_unitary_links(ctx):
     arr = np.ascontiguousarray(links)
     rc = abi.lib().tsm_create_gauge(ctx.handle, dims_c, arr.ctypes.data_as(ctypes.c_void_p), -1, 1, ctypes.byref(h))
     assert rc == abi.TSM_ERR_NONFINITE
+
+
+# The Schur operator is two half-volume hops with a stored intermediate, so
+# its 16-bit error budget is twice the single operator's.
+TOL_MHAT = {abi.TSM_F64: 1e-13, abi.TSM_F32: 4e-6, abi.TSM_F16: 6e-3, abi.TSM_BF16: 6e-2}
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (8, 6, 4, 10), (2, 4, 2, 2)])
+@pytest.mark.parametrize("t_bc", [-1, 1])
+@pytest.mark.parametrize("prec", [abi.TSM_F64, abi.TSM_F32, abi.TSM_F16, abi.TSM_BF16])
+def test_schur_operator_matches_oracle(ctx, dims, t_bc, prec):
+    from oracle import evenodd
+    kappa, mu = 0.13, 0.07
+    g, links = gauge(ctx, dims, 0.35, 21, t_bc)
+    u = lattice.effective_links(links, t_bc)
+    psi = round_to(synth.gaussian_spinor(dims, 22, nrhs=2), prec)
+    nat = g.pack(to_device(psi), prec)
+    for op, fn in ((abi.TSM_OP_MHAT, evenodd.apply_mhat), (abi.TSM_OP_MHATDAG, evenodd.apply_mhat_dag)):
+        out = g.unpack(g.dslash(op, kappa, mu, prec, nat, 2), prec, 2).cpu().numpy()
+        for r in range(2):
+            want = fn(u, psi[r], dims, kappa, mu)
+            _check(out[r], want, TOL_MHAT[prec])
+            assert np.all(evenodd.restrict(out[r], dims, 0) == 0)
+    g.close()
+
+
+@pytest.mark.parametrize("dims", [(3, 4, 2, 2), (4, 3, 2, 2), (4, 4, 2, 3)])
+def test_schur_operator_rejects_odd_extents(ctx, dims):
+    g, _ = gauge(ctx, dims, 0.3, 1, -1, precs=(abi.TSM_F64,))
+    nat = g.pack(to_device(synth.gaussian_spinor(dims, 1, nrhs=1)), abi.TSM_F64)
+    with pytest.raises(abi.TsmError):
+        g.dslash(abi.TSM_OP_MHAT, 0.1, 0.1, abi.TSM_F64, nat, 1)
+    g.close()

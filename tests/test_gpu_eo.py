@@ -138,11 +138,12 @@ def test_eo_tsm_lowprec(ctx):
 
 
 def test_eo_argument_checks(ctx):
-    g, _ = gauge(ctx, (3, 4, 2, 4), 0.3, 1, -1)
-    with pytest.raises(abi.TsmError) as e:
-        g.solve_sources(0.125, 0.01, abi.TSM_SOLVER_F64 | EO, 1e-8, 1, 0, 1)
-    assert e.value.code == abi.TSM_ERR_INVALID_ARG
-    g.close()
+    for dims in ((3, 4, 2, 4), (4, 4, 2, 5), (4, 3, 2, 4)):
+        g, _ = gauge(ctx, dims, 0.3, 1, -1)
+        with pytest.raises(abi.TsmError) as e:
+            g.solve_sources(0.125, 0.01, abi.TSM_SOLVER_F64 | EO, 1e-8, 1, 0, 1)
+        assert e.value.code == abi.TSM_ERR_INVALID_ARG
+        g.close()
     g, _ = gauge(ctx, (4, 4, 2, 4), 0.3, 1, -1)
     inst = dict(gauge=g, kappa=0.125, mu=0.01, noise_seed=1, first_src=0, nsrc=1)
     with pytest.raises(abi.TsmError):

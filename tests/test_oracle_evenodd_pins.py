@@ -28,8 +28,11 @@ def _index_sets(dims):
 def test_parity_checkerboard():
     par = evenodd.parity((4, 2, 2, 2))
     assert par.shape == (2, 2, 2, 4) and par.sum() * 2 == par.size
-    # the x-neighbour always has the other parity
-    assert np.all(np.roll(par, 1, axis=-1) != par)
+    # every neighbour, across the periodic wrap too, has the other parity
+    for axis in (-1, -2, -3, -4):
+        assert np.all(np.roll(par, 1, axis=axis) != par)
+    with pytest.raises(ValueError):
+        evenodd.parity((4, 3, 2, 2))
 
 
 @pytest.mark.parametrize("mu", [0.0, 0.07])
