@@ -82,7 +82,11 @@ static int bind(const tsm_gauge* g) {
 
 }  // namespace tsm
 
-tsm_gauge::~tsm_gauge() {}
+tsm_gauge::~tsm_gauge() {
+  if (aux_stream) cudaStreamDestroy(aux_stream);
+  for (cudaEvent_t e : aux_ev)
+    if (e) cudaEventDestroy(e);
+}
 
 using namespace tsm;
 

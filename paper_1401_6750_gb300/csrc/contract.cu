@@ -386,8 +386,8 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
 }  // namespace
 
 struct ContractWorkspace {
+  std::mutex mu;  // held for a whole contraction
   DevBuf v, fields, part, mom;
-  bool gamma_ready = false;
 };
 
 void ContractWsDeleter::operator()(ContractWorkspace* w) const { delete w; }
@@ -438,7 +438,8 @@ int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsr
 }  // namespace
 
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
-                   const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
+                   const int* mom_host, double* out_dev, int accumulate, cudaStream_t st, int slot) {
+  if (slot < 0 || slot > 1) return fail(TSM_ERR_INVALID_ARG, "workspace slot %d", slot);
   if (prec != TSM_F32 && prec != TSM_F64)
     return fail(TSM_ERR_INVALID_ARG, "contraction takes F32 or F64 solutions, got precision %d", prec);
   if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
@@ -449,15 +450,20 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
       if (n > 8 || n < -8) return fail(TSM_ERR_INVALID_ARG, "momentum component %d outside [-8, 8]", n);
       rad = std::max(rad, n < 0 ? -n : n);
     }
-  std::lock_guard<std::mutex> lock(g->mu);
-  if (!g->contract_ws) g->contract_ws.reset(new ContractWorkspace());
-  ContractWorkspace& w = *g->contract_ws;
-  if (!w.gamma_ready) {
-    GammaTable t;
-    TSM_TRY(build_gamma_table(t));
-    TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
-    w.gamma_ready = true;
+  ContractWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    if (!g->contract_ws[slot]) g->contract_ws[slot].reset(new ContractWorkspace());
+    wp = g->contract_ws[slot].get();
+    if (!g->gamma_ready) {
+      GammaTable t;
+      TSM_TRY(build_gamma_table(t));
+      TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+      g->gamma_ready = true;
+    }
   }
+  ContractWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
   const int V = g->geom.V;
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2], lt = g->geom.L[3];

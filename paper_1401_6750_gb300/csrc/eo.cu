@@ -81,6 +81,7 @@ __global__ void k_diag(void* out, const void* in, double cr, double ci, int vh) 
 }  // namespace
 
 struct EoWorkspace {
+  std::mutex mu;  // held for a whole solve
   int cap = 0, nblk = 0;
   DevBuf st, partial, counter, mask, b, t1, tep, eta_e, x, r, p, q, tes, xacc, full;
   RhsState* h_st = nullptr;
@@ -448,12 +449,17 @@ struct SolverEO {
 template <int KIND>
 int solve_eo_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_iter, int nrhs, const void* eta,
                   int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out, int gamma5_io,
-                  tsm_solve_stats* stats, cudaStream_t s) {
+                  tsm_solve_stats* stats, cudaStream_t s, int slot) {
   using T = Traits<KIND>;
-  std::lock_guard<std::mutex> lock(g->mu);
-  auto& slot = g->eo_ws[KIND];
-  if (!slot) slot.reset(new EoWorkspace());
-  EoWorkspace& w = *slot;
+  EoWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    auto& ws = g->eo_ws[KIND + 64 * slot];
+    if (!ws) ws.reset(new EoWorkspace());
+    wp = ws.get();
+  }
+  EoWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
   TSM_TRY(SolverEO<KIND>::reserve(g, w, nrhs));
   if (eta) {
     TSM_TRY(spinor_convert(g, T::PP, w.full.p, eta_prec, eta, nrhs, gamma5_io, s));
@@ -531,21 +537,21 @@ int schur_apply(tsm_gauge* g, int prec, int dag, double kappa, double mu, const 
 
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                    const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
-                   int gamma5_io, tsm_solve_stats* stats, cudaStream_t s) {
+                   int gamma5_io, tsm_solve_stats* stats, cudaStream_t s, int slot) {
   if (!eo_lattice(g->geom)) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need even extents");
   switch (solver & ~TSM_SOLVER_EO) {
     case TSM_SOLVER_F64:
       return solve_eo_kind<TSM_SOLVER_F64>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec,
-                                           x_out, gamma5_io, stats, s);
+                                           x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_F32_RELIABLE:
       return solve_eo_kind<TSM_SOLVER_F32_RELIABLE>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                                    out_prec, x_out, gamma5_io, stats, s);
+                                                    out_prec, x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_LP_F16:
       return solve_eo_kind<TSM_SOLVER_LP_F16>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                              out_prec, x_out, gamma5_io, stats, s);
+                                              out_prec, x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_LP_BF16:
       return solve_eo_kind<TSM_SOLVER_LP_BF16>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                               out_prec, x_out, gamma5_io, stats, s);
+                                               out_prec, x_out, gamma5_io, stats, s, slot);
   }
   return fail(TSM_ERR_INVALID_ARG, "unknown solver %d", solver);
 }

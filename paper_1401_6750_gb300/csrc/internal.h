@@ -99,14 +99,20 @@ struct tsm_gauge {
   unsigned precisions = 0;
   tsm::DevBuf links[5];  // indexed by precision (TSM_DS: float-float twin of the FP64 copy)
   std::mutex mu;  // guards the caches below
+  // workspaces keyed by solver kind + 64 * slot; slot 1 serves the TSM
+  // driver's second stream, so two solves of one kind can run at once
   std::map<long long, std::unique_ptr<tsm::SolverWorkspace, tsm::SolverWsDeleter>> solver_ws;
   std::map<long long, std::unique_ptr<tsm::EoWorkspace, tsm::EoWsDeleter>> eo_ws;
-  std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws;
+  std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws[2];
+  bool gamma_ready = false;  // insertion table uploaded (guarded by mu)
   tsm::DevBuf tmp;  // operator scratch (M^dag M intermediate, conversions)
   tsm::DevBuf eo_tmp;  // Schur operator scratch (three half-volume fields; guarded by mu)
   std::mutex tsm_mu;       // guards the TSM buffers
   tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
   tsm::DevBuf tsm_sol;     // solutions of one batch
+  tsm::DevBuf tsm_sol2;    // the same for the second stream
+  cudaStream_t aux_stream = nullptr;   // the TSM driver's second stream
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};  // fork and join events
   std::mutex grad_mu;      // guards grad_ws
   std::unique_ptr<tsm::GradWorkspace, tsm::GradWsDeleter> grad_ws;
   std::mutex tune_mu;      // guards nr_cache
@@ -150,14 +156,16 @@ int build_links(tsm_gauge* g, const double* links_host);
 // Solve M(mu) x = eta for nrhs right-hand sides.  eta (device, native layout of
 // eta_prec) or, when eta is null, the Z4 sources (seed, first .. first+nrhs-1).
 // gamma5_io != 0 multiplies eta by g5 on input and x by g5 on output.
+// `slot` selects one of two workspace sets, so that solves on two streams can
+// run at once (0 for every public entry point).
 int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                      const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
-                     int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
+                     int gamma5_io, tsm_solve_stats* stats, cudaStream_t s, int slot = 0);
 int solver_precise_prec(int solver);
 // The same with the even-odd preconditioned CG (solver carries TSM_SOLVER_EO; eo.cu).
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                    const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
-                   int gamma5_io, tsm_solve_stats* stats, cudaStream_t s);
+                   int gamma5_io, tsm_solve_stats* stats, cudaStream_t s, int slot);
 // out = Mhat in (dag: Mhat^dag) on the odd sites of full-layout fields, zero on
 // the even sites (eo.cu)
 int schur_apply(tsm_gauge* g, int prec, int dag, double kappa, double mu, const void* in, void* out, int nrhs,
@@ -176,7 +184,7 @@ unsigned solver_link_precs(int solver);
 
 // ---- contraction (contract.cu)
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
-                   const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
+                   const int* mom_host, double* out_dev, int accumulate, cudaStream_t s, int slot = 0);
 int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                            const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 

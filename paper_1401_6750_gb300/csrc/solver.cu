@@ -41,6 +41,7 @@ using namespace solverk;
 
 // ---------------------------------------------------------------- workspace
 struct SolverWorkspace {
+  std::mutex mu;  // held for a whole solve
   int kind = -1;
   int cap = 0;  // right-hand sides allocated
   int nblk = 0;
@@ -360,12 +361,17 @@ struct Solver {
 template <int KIND>
 int solve_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_iter, int nrhs, const void* eta,
                int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out, int gamma5_io,
-               tsm_solve_stats* stats, cudaStream_t s) {
+               tsm_solve_stats* stats, cudaStream_t s, int slot) {
   using T = Traits<KIND>;
-  std::lock_guard<std::mutex> lock(g->mu);
-  auto& slot = g->solver_ws[KIND];
-  if (!slot) slot.reset(new SolverWorkspace());
-  SolverWorkspace& w = *slot;
+  SolverWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    auto& ws = g->solver_ws[KIND + 64 * slot];
+    if (!ws) ws.reset(new SolverWorkspace());
+    wp = ws.get();
+  }
+  SolverWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
   w.kind = KIND;
   TSM_TRY(Solver<KIND>::reserve(g, w, nrhs));
   if (eta) {
@@ -381,27 +387,28 @@ int solve_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_iter, 
 // eta == nullptr: Z4 sources (seed, first) are generated in place.
 int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                      const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
-                     int gamma5_io, tsm_solve_stats* stats, cudaStream_t s) {
+                     int gamma5_io, tsm_solve_stats* stats, cudaStream_t s, int slot) {
+  if (slot < 0 || slot > 1) return fail(TSM_ERR_INVALID_ARG, "workspace slot %d", slot);
   const unsigned need = solver_link_precs(solver);
   if ((g->precisions & need) != need)
     return fail(TSM_ERR_INVALID_ARG, "solver %d needs gauge copies 0x%x, gauge has 0x%x", solver, need,
                 g->precisions);
   if (solver & TSM_SOLVER_EO)
     return solve_batch_eo(g, kappa, mu, solver, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec, x_out,
-                          gamma5_io, stats, s);
+                          gamma5_io, stats, s, slot);
   switch (solver) {
     case TSM_SOLVER_F64:
       return solve_kind<TSM_SOLVER_F64>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first, out_prec,
-                                        x_out, gamma5_io, stats, s);
+                                        x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_F32_RELIABLE:
       return solve_kind<TSM_SOLVER_F32_RELIABLE>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                                 out_prec, x_out, gamma5_io, stats, s);
+                                                 out_prec, x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_LP_F16:
       return solve_kind<TSM_SOLVER_LP_F16>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                           out_prec, x_out, gamma5_io, stats, s);
+                                           out_prec, x_out, gamma5_io, stats, s, slot);
     case TSM_SOLVER_LP_BF16:
       return solve_kind<TSM_SOLVER_LP_BF16>(g, kappa, mu, rho, max_iter, nrhs, eta, eta_prec, seed, first,
-                                            out_prec, x_out, gamma5_io, stats, s);
+                                            out_prec, x_out, gamma5_io, stats, s, slot);
   }
   return fail(TSM_ERR_INVALID_ARG, "unknown solver %d", solver);
 }

@@ -13,8 +13,12 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <chrono>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -44,11 +48,27 @@ struct Accum {
       not_conv += !st[k].converged;
     }
   }
+  void merge(const Accum& o) {
+    iters_total += o.iters_total;
+    iters_max = std::max(iters_max, o.iters_max);
+    res_max = std::max(res_max, o.res_max);
+    not_conv += o.not_conv;
+  }
 };
+
+// The correction solves run on a second stream, beside the bulk, unless
+// TSM_STREAMS=1 (measurements) or the per-kernel profiler is on.
+bool concurrent_correction() {
+  static const bool on = [] {
+    const char* e = getenv("TSM_STREAMS");
+    return !(e && atoi(e) == 1);
+  }();
+  return on && !profiling();
+}
 
 // Solve sources [first, first + n) with `solver` and add their loops to acc.
 int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho, uint64_t first, int n,
-                       int batch, DevBuf& sol, double* acc, Accum& a, cudaStream_t s) {
+                       int batch, DevBuf& sol, double* acc, Accum& a, cudaStream_t s, int slot) {
   // loops are contracted in FP64 for the all-FP64 solver and in FP32 otherwise
   const int op = (solver_kind(solver) == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
   std::vector<tsm_solve_stats> st(batch);
@@ -56,10 +76,10 @@ int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho
     const int nb = std::min(batch, n - k0);
     TSM_TRY(sol.reserve(tsm_spinor_bytes(g, op, nb)));
     int rc = solve_batch_impl(g, p->kappa, p->mu, solver, rho, p->max_iter, nb, nullptr, 0, p->noise_seed,
-                              first + k0, op, sol.p, 0, st.data(), s);
+                              first + k0, op, sol.p, 0, st.data(), s, slot);
     if (rc != TSM_OK && rc != TSM_ERR_NOT_CONVERGED) return rc;
     a.add(st, nb);
-    TSM_TRY(contract_loops(g, p->kappa, p->mu, op, sol.p, nb, p->n_mom, p->mom, acc, 1, s));
+    TSM_TRY(contract_loops(g, p->kappa, p->mu, op, sol.p, nb, p->n_mom, p->mom, acc, 1, s, slot));
   }
   return TSM_OK;
 }
@@ -102,13 +122,49 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
   double* lpc = hp + n_out;
   double* est = est_dev ? est_dev : lpc + n_out;
   TSM_CUDA(cudaMemsetAsync(bulk, 0, sizeof(double) * n_out * 3, s));
-  Accum lp_a, hp_a;
-  DevBuf& sol = g->tsm_sol;
-  TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, 0, p->n_lp, batch, sol, bulk, lp_a, s));
-  if (p->n_hp > 0) {
-    TSM_TRY(solve_and_contract(g, p, p->hp_solver, p->rho_hp, (uint64_t)p->n_lp, p->n_hp, batch, sol, hp, hp_a, s));
-    TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, (uint64_t)p->n_lp, p->n_hp, batch, sol, lpc, lp_a, s));
+  Accum lp_a, hp_a, lpc_a;
+  const uint64_t c0 = (uint64_t)p->n_lp;
+  if (p->n_hp == 0 || !concurrent_correction()) {
+    TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, 0, p->n_lp, batch, g->tsm_sol, bulk, lp_a, s, 0));
+    if (p->n_hp > 0) {
+      TSM_TRY(solve_and_contract(g, p, p->hp_solver, p->rho_hp, c0, p->n_hp, batch, g->tsm_sol, hp, hp_a, s, 0));
+      TSM_TRY(solve_and_contract(g, p, p->lp_solver, p->rho_lp, c0, p->n_hp, batch, g->tsm_sol, lpc, lpc_a, s, 0));
+    }
+  } else {
+    // The correction sources' HP and LP solves (small batches whose kernels
+    // leave HBM and SMs partly idle) run on a second stream from a worker
+    // thread, beside the bulk LP solves on the caller's stream.  Each side
+    // has its own workspaces (slot 1) and solution buffer; the host waits of
+    // the solvers' convergence checks happen in each thread independently.
+    if (!g->aux_stream) {
+      TSM_CUDA(cudaStreamCreateWithFlags(&g->aux_stream, cudaStreamNonBlocking));
+      TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[0], cudaEventDisableTiming));
+      TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[1], cudaEventDisableTiming));
+    }
+    cudaStream_t s2 = g->aux_stream;
+    TSM_CUDA(cudaEventRecord(g->aux_ev[0], s));  // accumulators cleared
+    TSM_CUDA(cudaStreamWaitEvent(s2, g->aux_ev[0], 0));
+    int rc2 = TSM_OK;
+    std::string err2;
+    std::thread worker([&] {
+      const cudaError_t e = cudaSetDevice(g->ctx->device);
+      if (e != cudaSuccess) {
+        rc2 = cuda_status(e, "cudaSetDevice", __FILE__, __LINE__);
+      } else {
+        rc2 = solve_and_contract(g, p, p->hp_solver, p->rho_hp, c0, p->n_hp, batch, g->tsm_sol2, hp, hp_a, s2, 1);
+        if (rc2 == TSM_OK)
+          rc2 = solve_and_contract(g, p, p->lp_solver, p->rho_lp, c0, p->n_hp, batch, g->tsm_sol2, lpc, lpc_a, s2, 1);
+      }
+      if (rc2 != TSM_OK) err2 = tsm_last_error();  // the message is thread-local
+    });
+    const int rc1 = solve_and_contract(g, p, p->lp_solver, p->rho_lp, 0, p->n_lp, batch, g->tsm_sol, bulk, lp_a, s, 0);
+    worker.join();
+    TSM_CUDA(cudaEventRecord(g->aux_ev[1], s2));  // the caller's stream continues after both
+    TSM_CUDA(cudaStreamWaitEvent(s, g->aux_ev[1], 0));
+    if (rc1 != TSM_OK) return rc1;
+    if (rc2 != TSM_OK) return fail(rc2, "%s", err2.c_str());
   }
+  lp_a.merge(lpc_a);
   const int bs = 256;
   count_launches(1);
   combine_kernel<<<(unsigned)((n_out + bs - 1) / bs), bs, 0, s>>>(bulk, hp, lpc, 1.0 / p->n_lp,
