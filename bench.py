@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-equal-accuracy", action="store_true")
+    ap.add_argument("--no-tdil", action="store_true", help="skip the time-dilution measurement")
     ap.add_argument("--probe", default=None, choices=["dslash", "tsm"],
                     help="run a few launches of one kernel family for an ncu capture and exit")
     ap.add_argument("--probe-time", action="store_true", help="with --probe dslash: print event-timed GB/s")
@@ -346,6 +347,40 @@ def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs
             "note": "p = 0 loops summed over timeslices; variances from per-source samples"}
 
 
+def time_dilution(g, abi, torch, w, lp_solver, moms, reps=3):
+    """The time-dilution workload (Sec. 2.2) on the same lattice: the T
+    diluted sources of one noise vector, solved together by the LP map and
+    contracted with the standard estimator on their own timeslices.  Timed
+    with CUDA events on the current stream, after one warm-up pass."""
+    import ctypes
+    T = g.dims[3]
+    stream = torch.cuda.current_stream()
+    kind = lp_solver & ~abi.TSM_SOLVER_EO
+    prec = abi.TSM_F64 if kind in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+    t0 = list(range(T))
+    out = torch.zeros((abi.TSM_N_INSERTIONS, len(moms), T, 2), dtype=torch.float64, device="cuda")
+    times, t_solve, iters = [], [], []
+    for rep in range(reps + 1):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        eta = g.diluted_sources(1017, rep, 0, T, prec)
+        sol, st = g.invert(abi.TSM_OP_M, w["kappa"], w["mu"], lp_solver, w["rho_lp"], eta, T)
+        e1.record(stream)
+        g.contract_tdil(prec, sol, eta, T, t0, moms, out=out, accumulate=rep > 0)
+        e2.record(stream)
+        e2.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e2) * 1e-3)
+            t_solve.append(e0.elapsed_time(e1) * 1e-3)
+            iters.append(sum(x["iterations"] for x in st) / T)
+    t = sorted(times)[len(times) // 2]
+    return {"workload": "one Z4 noise vector diluted over all %d timeslices (%d sources), LP map, standard "
+                        "estimator on each source's timeslice" % (T, T),
+            "diluted_sources_per_s": T / t, "noise_vectors_per_s": 1.0 / t, "ms_per_noise_vector": t * 1e3,
+            "solve_share": sorted(t_solve)[len(t_solve) // 2] / t, "lp_iterations_mean": sum(iters) / len(iters),
+            "reps": reps}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -491,6 +526,10 @@ def main():
     if rank == 0 and not args.no_equal_accuracy:
         eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver)
 
+    tdil = None
+    if rank == 0 and not args.no_tdil:
+        tdil = time_dilution(g, abi, torch, w, lp_solver, moms)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(dims, w["kappa"], w["mu"], ORACLE_LP_ITERS, n_mom)
@@ -518,6 +557,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "equal_accuracy": eq,
+            "time_dilution": tdil,
         }
         print(json.dumps(line), flush=True)
     g.close()

@@ -155,6 +155,16 @@ int tsm_dslash_tm(tsm_gauge* g, double kappa, double mu, int op, int prec,
 int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src,
                      int nsrc, int prec, void* out_dev, void* stream);
 
+/* Time dilution (Sec. 2.2): n_t fields, field k being the Z4 source of
+ * (noise_seed, source_id) -- the same values tsm_make_sources gives for
+ * first_src = source_id -- kept on timeslice t_first + k and zero on every
+ * other timeslice, so the T diluted sources of one noise vector sum to the
+ * volume source.  Needs 0 <= t_first and t_first + n_t <= T.  Written in
+ * native layout of `prec` (F64, F32, F16 or BF16). */
+int tsm_make_diluted_sources(tsm_gauge* g, uint64_t noise_seed,
+                             uint64_t source_id, int t_first, int n_t,
+                             int prec, void* out_dev, void* stream);
+
 /* Solve M s_r = eta_r (Eq. 1) for the Z4 sources r = first_src ..
  * first_src + nsrc - 1 by CG on M^dag M with x0 = 0, stopping when the
  * iterated residual of the normal equations drops below rho and the true
@@ -233,6 +243,25 @@ int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec,
                        const double* grad_dev, int solver, double rho,
                        int max_iter, double* dmu_host, void* grad_eta_dev,
                        void* stream);
+
+/* Loops of the 160 insertions from the standard estimator, for sources that
+ * are time-diluted (the paper's single-timeslice contraction, Sec. 2.2) or
+ * not: for nsrc sources eta_r and their solutions s_r = M(mu)^{-1} eta_r
+ * (both native F64 or F32 fields, nsrc each), the bilinear
+ * psibar(y) K psi(z) -> Tr[K G(z, y)] is estimated by eta(y)^dag K s(z) for
+ * the u flavour and, through g5-hermiticity (G_d = g5 G_u^dag g5), by
+ * conj(eta(z)^dag g5 K^dag g5 s(y)) for the d flavour; insertion f*80 + i
+ * carries u - d (f = 0, with tau_3) or u + d (f = 1), with the insertion
+ * index, derivative form and layout [160][n_mom][T][2] of tsm_contract_loops,
+ * summed (not averaged) over the sources.  t0_host (optional, nsrc values)
+ * gives each source's timeslice, or -1 for a volume source; only the
+ * timeslices a source touches are contracted (t0, and t0 - 1 for the time
+ * derivative).  The momentum list must hold -p with every p.  accumulate != 0
+ * adds to out_dev.  Asynchronous on `stream`. */
+int tsm_contract_tdil(tsm_gauge* g, int prec, const void* s_dev,
+                      const void* eta_dev, int nsrc, const int* t0_host,
+                      int n_mom, const int* mom, double* out_dev,
+                      int accumulate, void* stream);
 
 /* Allocation-free variant of tsm_contract_loops (the paper has no
  * counterpart: it is an interface convenience).  It is meant for callers

@@ -137,6 +137,30 @@ class Gauge:
                                                _ptr(out), int(accumulate), _stream(stream)), "tsm_contract_loops")
         return out
 
+    def diluted_sources(self, noise_seed, source_id, t_first, n_t, prec, stream=None):
+        """Time dilution: the Z4 source (noise_seed, source_id) on timeslices
+        t_first .. t_first + n_t - 1, one field each."""
+        out = self.empty_native(prec, n_t)
+        abi.check(abi.lib().tsm_make_diluted_sources(self.handle, noise_seed, source_id, t_first, n_t, prec,
+                                                     _ptr(out), _stream(stream)), "tsm_make_diluted_sources")
+        return out
+
+    def contract_tdil(self, prec, native_s, native_eta, nsrc, t0, moms, out=None, accumulate=False, stream=None):
+        """Standard-estimator loops (summed over the sources) of sources eta with
+        timeslices t0 (-1: volume source) and their solutions s."""
+        moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        n_mom = moms.shape[0]
+        if out is None:
+            out = torch.zeros((abi.TSM_N_INSERTIONS, n_mom, self.dims[3], 2), dtype=torch.float64, device="cuda")
+        t0_c = None
+        if t0 is not None:
+            t0_a = np.ascontiguousarray(np.asarray(t0, dtype=np.int32))
+            t0_c = t0_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        abi.check(abi.lib().tsm_contract_tdil(self.handle, prec, _ptr(native_s), _ptr(native_eta), nsrc, t0_c, n_mom,
+                                              moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(out),
+                                              int(accumulate), _stream(stream)), "tsm_contract_tdil")
+        return out
+
     def tsm(self, kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp_solver, hp_solver, noise_seed, moms, max_iter=100000,
             nrhs_per_launch=12, want_parts=False, stream=None):
         moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))

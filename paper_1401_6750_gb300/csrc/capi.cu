@@ -241,6 +241,26 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src, int 
   return make_sources(g, noise_seed, first_src, nsrc, prec, out_dev, pick_stream(g, stream));
 }
 
+int tsm_make_diluted_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t source_id, int t_first, int n_t, int prec,
+                             void* out_dev, void* stream) {
+  if (!g || !out_dev || !valid_prec(prec) || n_t < 0 || n_t > 65535 || t_first < 0 ||
+      t_first + n_t > g->geom.L[3])
+    return fail(TSM_ERR_INVALID_ARG, "tsm_make_diluted_sources: bad argument");
+  if (n_t == 0) return TSM_OK;
+  TSM_TRY(bind(g));
+  return make_diluted_sources(g, noise_seed, source_id, t_first, n_t, prec, out_dev, pick_stream(g, stream));
+}
+
+int tsm_contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
+                      int n_mom, const int* mom, double* out_dev, int accumulate, void* stream) {
+  if (!g || !s_dev || !eta_dev || !out_dev || nsrc < 0 || nsrc > 65535 || n_mom < 1 || n_mom > 4096 || !mom)
+    return fail(TSM_ERR_INVALID_ARG, "tsm_contract_tdil: bad argument");
+  if (nsrc == 0 && accumulate) return TSM_OK;
+  TSM_TRY(bind(g));
+  return contract_tdil(g, prec, s_dev, eta_dev, nsrc, t0_host, n_mom, mom, out_dev, accumulate,
+                       pick_stream(g, stream));
+}
+
 static int check_solver_args(const tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter) {
   if (!g) return fail(TSM_ERR_INVALID_ARG, "gauge is NULL");
   if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver %d", solver);

@@ -228,15 +228,15 @@ __device__ __forceinline__ void twiddle(cplx<double>& o, int m, int L) {
   o = mk<double>(cs, -sn);
 }
 
-// x then y transform of the 160 site fields of one (z, t) plane:
+// x then y transform of the nfields site fields of one (z, t) plane:
 //   part[plane][(n_x, n_y)][f] = sum_{x,y} F_f(x, y) e^{-2 pi i (n_x x / Lx + n_y y / Ly)}
-// in chunks of nfc fields (a divisor of 160 sized to shared memory).  x: one thread per (field, row) reads the row
+// in chunks of nfc fields (a divisor of nfields sized to shared memory).  x: one thread per (field, row) reads the row
 // once from global memory and keeps XY_NC momenta in flight; y: one thread
 // per (field, n_x) over the rows in shared memory; the chunk's results are
 // staged so that the stores run along f.
 template <typename R>
 __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __restrict__ F, Geom g, int rad,
-                                                            int nfc, double2* __restrict__ part) {
+                                                            int nfc, int nfields, double2* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lx = g.L[0], ly = g.L[1];
   const int nx = 2 * rad + 1, nxy = nx * nx;
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
   }
   const size_t V = (size_t)g.V;
   const cplx<R>* Fp = F + (size_t)plane * lx * ly;
-  for (int f0 = 0; f0 < 5 * NF; f0 += nfc) {
+  for (int f0 = 0; f0 < nfields; f0 += nfc) {
     __syncthreads();
     for (int task = threadIdx.x; task < nfc * ly; task += blockDim.x) {
       const int row = task % ly, f = task / ly;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
     __syncthreads();
     for (int k = threadIdx.x; k < nxy * nfc; k += blockDim.x) {
       const int f = k % nfc, nn = k / nfc;
-      part[((size_t)plane * nxy + nn) * 160 + f0 + f] = make_double2((double)Y[k].re, (double)Y[k].im);
+      part[((size_t)plane * nxy + nn) * nfields + f0 + f] = make_double2((double)Y[k].re, (double)Y[k].im);
     }
   }
 }
@@ -383,11 +383,193 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
   }
 }
 
+// ---------------------------------------------------------------- standard estimator (time dilution)
+// For sources eta (a Z4 volume source, or one kept on a single timeslice:
+// time dilution) and their solutions s = M(mu)^{-1} eta, the bilinear
+// psibar(y) K psi(z) is estimated by eta(y)^dag K s(z) for the u flavour and,
+// through g5-hermiticity, by conj(eta(z)^dag g5 K^dag g5 s(y)) for the d
+// flavour.  Both need, per site, only the open 4x4 matrices (no g5 factor)
+//   M[a][b]     = sum_c conj(eta_ac(x)) s_bc(x)
+//   D_mu[a][b]  = 1/4 sum_c [conj(eta_ac(x)) (U_mu(x) s(x+mu))_bc - conj(eta_ac(x+mu)) (U_mu(x)^dag s(x))_bc]
+// (the derivative's backward terms are D_mu at x - mu, applied after the
+// projection as in the one-end route).  A source on timeslice t0 touches
+// M and the F part of D on t0 and the G part of D_t on t0 - 1 only.
+template <typename R>
+struct TdilArgs {
+  Geom g;
+  const void* s;
+  const void* eta;
+  const void* links;
+  const int* t0;  // per source: its timeslice, or -1 for a volume source
+  int nsrc;
+  cplx<R>* F;     // [80][V]: pass * 16 + 4 a + b
+};
+
+template <typename R>
+__device__ __forceinline__ void matvec_dag(cplx<R> (&w)[12], const cplx<R> (&u)[3][3], const cplx<R> (&p)[12], R sgn) {
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      cplx<R> t = mk<R>(0, 0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) cmacc(t, u[b][a], p[3 * sp + b]);
+      w[3 * sp + a] = sgn * t;
+    }
+}
+
+template <typename R, int PS, int PL>
+__global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) tdil_fields_kernel(TdilArgs<R> a) {
+  const int pass = blockIdx.x % 5;
+  const int i = (blockIdx.x / 5) * FLD_BS + threadIdx.x;
+  if (i >= a.g.V) return;
+  const size_t V = (size_t)a.g.V;
+  int c[4];
+  site_coords(a.g, i, c);
+  cplx<R> m[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) m[k] = mk<R>(0, 0);
+  if (pass == 0) {
+    for (int r = 0; r < a.nsrc; ++r) {
+      const int t0 = a.t0[r];
+      if (t0 >= 0 && t0 != c[3]) continue;
+      cplx<R> e[12], x[12];
+      SpinorIO<PS>::load(a.eta, V, r, i, e);
+      SpinorIO<PS>::load(a.s, V, r, i, x);
+      outer<false>(m, e, x);
+    }
+  } else {
+    const int mu = pass - 1;
+    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    const int tn = (mu == 3) ? (c[3] + 1 == a.g.L[3] ? 0 : c[3] + 1) : c[3];
+    cplx<R> u[3][3];
+    LinkIO<PL>::load(a.links, V, mu, i, u);
+    const R sf = (mu == 3 && c[3] == a.g.L[3] - 1) ? (R)a.g.bc : (R)1;
+    for (int r = 0; r < a.nsrc; ++r) {
+      const int t0 = a.t0[r];
+      const bool f_on = t0 < 0 || t0 == c[3];
+      const bool g_on = t0 < 0 || t0 == tn;
+      cplx<R> e[12], x[12], w[12];
+      if (f_on) {  // conj(eta(x)) (U(x) s(x+mu))
+        SpinorIO<PS>::load(a.eta, V, r, i, e);
+        SpinorIO<PS>::load(a.s, V, r, nf, x);
+        matvec(w, u, x, sf);
+        outer<false>(m, e, w);
+      }
+      if (g_on) {  // - conj(eta(x+mu)) (U(x)^dag s(x))
+        SpinorIO<PS>::load(a.eta, V, r, nf, e);
+        SpinorIO<PS>::load(a.s, V, r, i, x);
+        matvec_dag(w, u, x, sf);
+        outer<true>(m, e, w);
+      }
+    }
+  }
+  const R scale = pass ? (R)0.25 : (R)1;
+  cplx<R>* out = a.F + (size_t)pass * 16 * V + i;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) out[(size_t)k * V] = scale * m[k];
+}
+
+// z transform, derivative shift and both flavours.  Block (t, group): group
+// 0 is M, group 1 + mu is D_mu.  u(p) = Gamma . Mt(p);  d(p) = +-conj(G' . Mt(-p))
+// with G' = g5 Gamma^dag g5 (+ for M, - for D); the derivative's shift is
+// the factor 1 + e^{-i p_mu} (spatial mu, applied to u and d at p) or the
+// sum of timeslices t and t - 1 (mu = t).  Outputs u - d (with tau_3) and
+// u + d (without).
+__global__ void __launch_bounds__(Z_BS) tdil_z_kernel(const double2* __restrict__ part, const int* __restrict__ mom,
+                                                      const int* __restrict__ mneg, int n_mom, Geom g, int rad,
+                                                      double* out, int accumulate) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lz = g.L[2], lt = g.L[3];
+  const int t = blockIdx.x, group = blockIdx.y;
+  const int nx = 2 * rad + 1, nxy = nx * nx;
+  double2* zs = reinterpret_cast<double2*>(smem_raw);  // [n_mom][16]
+  double2* twz = zs + (size_t)n_mom * 16;               // [nx][lz]
+  for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
+    const int n = q / lz - rad, zz = q % lz;
+    double sn, cs;
+    sincospi(2.0 * (double)(((n * zz) % lz + lz) % lz) / (double)lz, &sn, &cs);
+    twz[q] = make_double2(cs, -sn);
+  }
+  __syncthreads();
+  const int field0 = group * 16;
+  const int tm1 = (t + lt - 1) % lt;
+  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
+    const int m = q / 16, e = q % 16;
+    const int mx = mom[3 * m], my = mom[3 * m + 1], mz = mom[3 * m + 2];
+    const int nn = (mx + rad) * nx + (my + rad);
+    double re = 0.0, im = 0.0;
+    for (int zz = 0; zz < lz; ++zz) {
+      double2 p = part[((size_t)(zz + lz * t) * nxy + nn) * 80 + field0 + e];
+      if (group == 4) {
+        const double2 p1 = part[((size_t)(zz + lz * tm1) * nxy + nn) * 80 + field0 + e];
+        p.x += p1.x;
+        p.y += p1.y;
+      }
+      const double2 w = twz[(mz + rad) * lz + zz];
+      re += p.x * w.x - p.y * w.y;
+      im += p.x * w.y + p.y * w.x;
+    }
+    zs[q] = make_double2(re, im);
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
+    const int m = q / 16, gi = q % 16;
+    const int mb = mneg[m];
+    double ur = 0.0, ui = 0.0, dr = 0.0, di = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int b = c_gamma.col[gi][a];
+      const double vr = c_gamma.re[gi][a], vi = c_gamma.im[gi][a];
+      const double2 x = zs[m * 16 + 4 * a + b];
+      ur += vr * x.x - vi * x.y;
+      ui += vr * x.y + vi * x.x;
+      // g5 Gamma^dag g5 has conj(v) at (b, a), times g5_b g5_a
+      const double sg = ((a < 2) == (b < 2)) ? 1.0 : -1.0;
+      const double2 y = zs[mb * 16 + 4 * b + a];
+      dr += sg * (vr * y.x + vi * y.y);
+      di += sg * (vr * y.y - vi * y.x);
+    }
+    // d = +-conj(.)
+    const double sd = group == 0 ? 1.0 : -1.0;
+    dr = sd * dr;
+    di = -sd * di;
+    if (group >= 1 && group <= 3) {  // O(p) = (1 + e^{-2 pi i n_mu / L_mu}) D(p)
+      const int nmu = group == 1 ? mom[3 * m] : (group == 2 ? mom[3 * m + 1] : mom[3 * m + 2]);
+      const int L = g.L[group - 1];
+      double sn, cs;
+      sincospi(2.0 * (double)(((nmu % L) + L) % L) / (double)L, &sn, &cs);
+      const double fr = 1.0 + cs, fi = -sn;
+      double r2 = ur * fr - ui * fi, i2 = ur * fi + ui * fr;
+      ur = r2;
+      ui = i2;
+      r2 = dr * fr - di * fi;
+      i2 = dr * fi + di * fr;
+      dr = r2;
+      di = i2;
+    }
+    const int ins = group == 0 ? gi : 16 + 16 * (group - 1) + gi;
+    double* o0 = out + (((size_t)ins * n_mom + m) * lt + t) * 2;         // with tau_3: u - d
+    double* o1 = out + (((size_t)(80 + ins) * n_mom + m) * lt + t) * 2;  // without: u + d
+    if (accumulate) {
+      o0[0] += ur - dr;
+      o0[1] += ui - di;
+      o1[0] += ur + dr;
+      o1[1] += ui + di;
+    } else {
+      o0[0] = ur - dr;
+      o0[1] = ui - di;
+      o1[0] = ur + dr;
+      o1[1] = ui + di;
+    }
+  }
+}
+
 }  // namespace
 
 struct ContractWorkspace {
   std::mutex mu;  // held for a whole contraction
-  DevBuf v, fields, part, mom;
+  DevBuf v, fields, part, mom, aux;
 };
 
 void ContractWsDeleter::operator()(ContractWorkspace* w) const { delete w; }
@@ -399,11 +581,27 @@ size_t xy_smem(const Geom& g, int rad, int nfc, size_t cs) {
   return cs * ((size_t)nfc * g.L[1] * nx + (size_t)nx * nx * nfc + (size_t)nx * (g.L[0] + g.L[1]));
 }
 
-// Largest chunk of fields (dividing 160) whose transform fits in 160 KB; 0 if none.
-int xy_chunk(const Geom& g, int rad, size_t cs) {
+// Largest chunk of fields (dividing nfields) whose transform fits in 160 KB; 0 if none.
+int xy_chunk(const Geom& g, int rad, size_t cs, int nfields) {
   for (int nfc : {32, 16, 8, 4, 2, 1})
-    if (xy_smem(g, rad, nfc, cs) <= 160 * 1024) return nfc;
+    if (nfields % nfc == 0 && xy_smem(g, rad, nfc, cs) <= 160 * 1024) return nfc;
   return 0;
+}
+
+// x/y transform of nfields site fields of type cplx<R> into part
+template <typename R>
+int launch_xy(tsm_gauge* g, int rad, const void* F, int nfields, double2* part, cudaStream_t st) {
+  const int nfc = xy_chunk(g->geom, rad, sizeof(cplx<R>), nfields);
+  if (nfc == 0)
+    return fail(TSM_ERR_INVALID_ARG, "plane %dx%d too large for the contraction", g->geom.L[0], g->geom.L[1]);
+  const size_t smem = xy_smem(g->geom, rad, nfc, sizeof(cplx<R>));
+  auto kern = contract_xy_kernel<R>;
+  TSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  count_launches(1);
+  kern<<<g->geom.L[2] * g->geom.L[3], XY_BS, smem, st>>>(static_cast<const cplx<R>*>(F), g->geom, rad, nfc,
+                                                          nfields, part);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
 }
 
 // Site fields then x/y transform; F holds 160 V fields of type cplx<R>.
@@ -417,21 +615,15 @@ int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsr
   a.links = g->links[PL].p;
   a.nsrc = nsrc;
   a.F = static_cast<cplx<R>*>(F);
-  const int nfc = xy_chunk(g->geom, rad, sizeof(cplx<R>));
-  if (nfc == 0)
-    return fail(TSM_ERR_INVALID_ARG, "plane %dx%d too large for the contraction", g->geom.L[0], g->geom.L[1]);
-  const size_t smem = xy_smem(g->geom, rad, nfc, sizeof(cplx<R>));
   const unsigned nblk = (unsigned)((g->geom.V + FLD_BS - 1) / FLD_BS);
-  count_launches(2);
+  count_launches(1);
   if (ev_f) TSM_TRY(ev_f->begin(st));
   contract_fields_kernel<R, PS, PL><<<nblk * 5, FLD_BS, 0, st>>>(a);
   if (ev_f) TSM_TRY(ev_f->end(st));
-  auto kern = contract_xy_kernel<R>;
-  TSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  if (ev_xy) TSM_TRY(ev_xy->begin(st));
-  kern<<<g->geom.L[2] * g->geom.L[3], XY_BS, smem, st>>>(a.F, g->geom, rad, nfc, part);
-  if (ev_xy) TSM_TRY(ev_xy->end(st));
   TSM_CUDA(cudaGetLastError());
+  if (ev_xy) TSM_TRY(ev_xy->begin(st));
+  TSM_TRY(launch_xy<R>(g, rad, a.F, 160, part, st));
+  if (ev_xy) TSM_TRY(ev_xy->end(st));
   return TSM_OK;
 }
 
@@ -517,6 +709,82 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
   return TSM_OK;
 }
 
+
+int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
+                  int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
+  if (prec != TSM_F32 && prec != TSM_F64)
+    return fail(TSM_ERR_INVALID_ARG, "contraction takes F32 or F64 fields, got precision %d", prec);
+  if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
+  const int lt = g->geom.L[3];
+  std::vector<int> t0(nsrc, -1);
+  if (t0_host)
+    for (int r = 0; r < nsrc; ++r) {
+      if (t0_host[r] < -1 || t0_host[r] >= lt) return fail(TSM_ERR_INVALID_ARG, "source %d: timeslice %d", r, t0_host[r]);
+      t0[r] = t0_host[r];
+    }
+  int rad = 0;
+  std::vector<int> mneg(n_mom);
+  for (int m = 0; m < n_mom; ++m) {
+    for (int d = 0; d < 3; ++d) {
+      const int n = mom_host[3 * m + d];
+      if (n > 8 || n < -8) return fail(TSM_ERR_INVALID_ARG, "momentum component %d outside [-8, 8]", n);
+      rad = std::max(rad, n < 0 ? -n : n);
+    }
+    mneg[m] = -1;
+    for (int k = 0; k < n_mom; ++k)
+      if (mom_host[3 * k] == -mom_host[3 * m] && mom_host[3 * k + 1] == -mom_host[3 * m + 1] &&
+          mom_host[3 * k + 2] == -mom_host[3 * m + 2])
+        mneg[m] = k;
+    if (mneg[m] < 0) return fail(TSM_ERR_INVALID_ARG, "the momentum list must hold -p with every p");
+  }
+  ContractWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    if (!g->contract_ws[0]) g->contract_ws[0].reset(new ContractWorkspace());
+    wp = g->contract_ws[0].get();
+    if (!g->gamma_ready) {
+      GammaTable t;
+      TSM_TRY(build_gamma_table(t));
+      TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+      g->gamma_ready = true;
+    }
+  }
+  ContractWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
+  const int V = g->geom.V;
+  const int nx = 2 * rad + 1;
+  const int lz = g->geom.L[2];
+  const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
+  TSM_TRY(w.fields.reserve((size_t)80 * V * cs));
+  TSM_TRY(w.part.reserve((size_t)lz * lt * 80 * nx * nx * sizeof(double2)));
+  TSM_TRY(w.mom.reserve(sizeof(int) * 3 * (size_t)n_mom));
+  TSM_TRY(w.aux.reserve(sizeof(int) * ((size_t)n_mom + nsrc)));
+  int* mneg_dev = w.aux.as<int>();
+  int* t0_dev = mneg_dev + n_mom;
+  TSM_CUDA(cudaMemcpyAsync(w.mom.p, mom_host, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, st));
+  TSM_CUDA(cudaMemcpyAsync(mneg_dev, mneg.data(), sizeof(int) * n_mom, cudaMemcpyHostToDevice, st));
+  TSM_CUDA(cudaMemcpyAsync(t0_dev, t0.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
+  const unsigned nblk = (unsigned)((V + FLD_BS - 1) / FLD_BS);
+  count_launches(1);
+  if (prec == TSM_F32) {
+    TdilArgs<float> a{g->geom, s_dev, eta_dev, g->links[TSM_F32].p, t0_dev, nsrc, w.fields.as<cplx<float>>()};
+    tdil_fields_kernel<float, TSM_F32, TSM_F32><<<nblk * 5, FLD_BS, 0, st>>>(a);
+    TSM_CUDA(cudaGetLastError());
+    TSM_TRY(launch_xy<float>(g, rad, w.fields.p, 80, w.part.as<double2>(), st));
+  } else {
+    TdilArgs<double> a{g->geom, s_dev, eta_dev, g->links[TSM_F64].p, t0_dev, nsrc, w.fields.as<cplx<double>>()};
+    tdil_fields_kernel<double, TSM_F64, TSM_F64><<<nblk * 5, FLD_BS, 0, st>>>(a);
+    TSM_CUDA(cudaGetLastError());
+    TSM_TRY(launch_xy<double>(g, rad, w.fields.p, 80, w.part.as<double2>(), st));
+  }
+  const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
+  TSM_CUDA(cudaFuncSetAttribute(tdil_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
+  count_launches(1);
+  tdil_z_kernel<<<dim3(lt, 5), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), mneg_dev, n_mom, g->geom,
+                                                   rad, out_dev, accumulate);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
 }  // namespace tsm
 
 // ---------------------------------------------------------------- allocation-free variant

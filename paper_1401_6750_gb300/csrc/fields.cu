@@ -83,13 +83,24 @@ __device__ __forceinline__ void philox4x64_10(uint64_t (&x)[4], uint64_t k0, uin
   }
 }
 
+// Z4 sources; with t_first >= 0, field r is the source `first` kept on
+// timeslice t_first + r (time dilution) and zero on every other timeslice.
 template <int P>
-__global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out) {
+__global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out, int t_first = -1, int vol3 = 1) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (i >= V) return;
+  const bool diluted = t_first >= 0;
+  if (diluted && i / vol3 != t_first + r) {
+    using R = ew_real<P>;
+    cplx<R> z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) z[k] = mk<R>(0, 0);
+    SpinorIO<P>::store(out, (size_t)V, r, i, z);
+    return;
+  }
   uint64_t x[4] = {(uint64_t)i, 0ull, 0ull, 0ull};
-  philox4x64_10(x, seed, first + (uint64_t)r);
+  philox4x64_10(x, seed, diluted ? first : first + (uint64_t)r);
   const uint64_t w = x[0];
   using R = ew_real<P>;
   cplx<R> v[12];
@@ -184,6 +195,23 @@ int build_links(tsm_gauge* g, const double* links_host) {
     TSM_CUDA(cudaGetLastError());
   }
   TSM_CUDA(cudaDeviceSynchronize());
+  return TSM_OK;
+}
+
+int make_diluted_sources(const tsm_gauge* g, uint64_t seed, uint64_t source_id, int t_first, int n_t, int prec,
+                         void* out, cudaStream_t s) {
+  const int V = g->geom.V;
+  const int vol3 = g->geom.L[0] * g->geom.L[1] * g->geom.L[2];
+  dim3 grid((V + BS - 1) / BS, n_t);
+  count_launches(1);
+  switch (prec) {
+    case TSM_F64: z4_kernel<TSM_F64><<<grid, BS, 0, s>>>(seed, source_id, V, out, t_first, vol3); break;
+    case TSM_F32: z4_kernel<TSM_F32><<<grid, BS, 0, s>>>(seed, source_id, V, out, t_first, vol3); break;
+    case TSM_F16: z4_kernel<TSM_F16><<<grid, BS, 0, s>>>(seed, source_id, V, out, t_first, vol3); break;
+    case TSM_BF16: z4_kernel<TSM_BF16><<<grid, BS, 0, s>>>(seed, source_id, V, out, t_first, vol3); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+  }
+  TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }
 

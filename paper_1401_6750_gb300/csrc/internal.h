@@ -143,6 +143,9 @@ int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, 
 
 // ---- fields (fields.cu)
 int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* out, cudaStream_t s);
+// n_t fields: the source `source_id` kept on timeslices t_first .. t_first + n_t - 1, one each
+int make_diluted_sources(const tsm_gauge* g, uint64_t seed, uint64_t source_id, int t_first, int n_t, int prec,
+                         void* out, cudaStream_t s);
 int spinor_pack(const tsm_gauge* g, int prec, const double* plain, void* native, int nrhs, double scale,
                 cudaStream_t s);
 int spinor_unpack(const tsm_gauge* g, int prec, const void* native, double* plain, int nrhs, double scale,
@@ -185,6 +188,10 @@ unsigned solver_link_precs(int solver);
 // ---- contraction (contract.cu)
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                    const int* mom_host, double* out_dev, int accumulate, cudaStream_t s, int slot = 0);
+// Standard-estimator loops of sources eta (time-diluted: t0[r] >= 0, or volume
+// sources: t0[r] = -1) and their solutions s (contract.cu)
+int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
+                  int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                            const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 
