@@ -381,6 +381,50 @@ def time_dilution(g, abi, torch, w, lp_solver, moms, reps=3):
             "reps": reps}
 
 
+def hpe_variance(g, abi, torch, w, lp_solver, n=16):
+    """Hopping parameter expansion against the plain standard estimator:
+    n volume Z4 sources solved by the LP map; per source, the p = 0 scalar
+    and g5 loops (summed over timeslices) of both flavour combinations, with
+    and without the expansion; their variances over the sources and the
+    event-timed cost of each contraction."""
+    import numpy as np
+    kind = lp_solver & ~abi.TSM_SOLVER_EO
+    prec = abi.TSM_F64 if kind in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
+    stream = torch.cuda.current_stream()
+    eta = g.sources(2017, 0, n, prec)
+    sol, _ = g.invert(abi.TSM_OP_M, w["kappa"], w["mu"], lp_solver, w["rho_lp"], eta, n)
+    field = g.native_bytes(prec, 1)
+    sel = {"scalar (tau3)": 0, "g5 (tau3)": 15, "scalar": 80, "g5": 95}
+    vals = {"plain": [], "hpe": []}
+    times = {"plain": [], "hpe": []}
+    mom = [(0, 0, 0)]
+    for j in range(n):
+        ej, sj = eta[j * field:(j + 1) * field], sol[j * field:(j + 1) * field]
+        for kind_, fn in (("plain", lambda: g.contract_tdil(prec, sj, ej, 1, None, mom)),
+                          ("hpe", lambda: g.contract_hpe(w["kappa"], w["mu"], prec, sj, ej, 1, None, mom))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            times[kind_].append(e0.elapsed_time(e1))
+            a = out.cpu().numpy()
+            vals[kind_].append([(a[i, 0, :, 0] + 1j * a[i, 0, :, 1]).sum() for i in sel.values()])
+    obs = []
+    for k, name in enumerate(sel):
+        vp = np.array([v[k] for v in vals["plain"]])
+        vh = np.array([v[k] for v in vals["hpe"]])
+        var_p = float(vp.real.var(ddof=1) + vp.imag.var(ddof=1))
+        var_h = float(vh.real.var(ddof=1) + vh.imag.var(ddof=1))
+        obs.append({"observable": name, "mean_plain": [float(vp.mean().real), float(vp.mean().imag)],
+                    "mean_hpe": [float(vh.mean().real), float(vh.mean().imag)], "var_plain": var_p,
+                    "var_hpe": var_h, "variance_ratio": var_p / var_h if var_h > 0 else None})
+    med = lambda x: sorted(x[1:])[len(x[1:]) // 2]
+    return {"sources": n, "estimator": "standard, volume Z4 sources, LP map", "observables": obs,
+            "ms_contract_plain": med(times["plain"]), "ms_contract_hpe": med(times["hpe"]),
+            "note": "variances per source of the p = 0 loops summed over timeslices"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -527,8 +571,10 @@ def main():
         eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver)
 
     tdil = None
+    hpe_var = None
     if rank == 0 and not args.no_tdil:
         tdil = time_dilution(g, abi, torch, w, lp_solver, moms)
+        hpe_var = hpe_variance(g, abi, torch, w, lp_solver)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -558,6 +604,7 @@ def main():
             "cpu_baseline": cpu,
             "equal_accuracy": eq,
             "time_dilution": tdil,
+            "hpe": hpe_var,
         }
         print(json.dumps(line), flush=True)
     g.close()

@@ -263,6 +263,21 @@ int tsm_contract_tdil(tsm_gauge* g, int prec, const void* s_dev,
                       int n_mom, const int* mom, double* out_dev,
                       int accumulate, void* stream);
 
+/* tsm_contract_tdil with the hopping parameter expansion (HPE, Sec. 2.3)
+ * for the 16 ultra-local insertions of both flavours: with M = A0 - kappa H
+ * (A0 = 1 + i mu' g5) and Y = A0^{-1} kappa H, G = sum_{k<4} Y^k A0^{-1} +
+ * Y^4 G; the exact diagonal of the first four terms (a constant per site,
+ * orders 0 and 2, computed in closed form) is added at p = 0 once per
+ * source on the timeslices it covers, and the remainder is estimated by
+ * eta^dag X (Y^4 s).  The derivative insertions are those of
+ * tsm_contract_tdil.  kappa, mu must be those of the solves; needs every
+ * extent >= 4 (shorter extents close paths of length < 4 around the
+ * lattice).  Same arguments and layout otherwise. */
+int tsm_contract_hpe(tsm_gauge* g, double kappa, double mu, int prec,
+                     const void* s_dev, const void* eta_dev, int nsrc,
+                     const int* t0_host, int n_mom, const int* mom,
+                     double* out_dev, int accumulate, void* stream);
+
 /* Allocation-free variant of tsm_contract_loops (the paper has no
  * counterpart: it is an interface convenience).  It is meant for callers
  * that cannot call cudaMalloc during the call -- e.g. code running under a

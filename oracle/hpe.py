@@ -121,3 +121,21 @@ def hpe_densities(u, eta, s, kappa, mu, exact_u=None, support=None, ultralocal_o
             ex = ex * keep[None, :, None, None, None]
         out = out + ex
     return out
+
+
+def exact_ultralocal_constant(dims, kappa, mu):
+    """The closed form of ``exact_ultralocal`` for lattices with every extent
+    >= 4, broadcast to every site: orders 0 and 2 of the expansion (pinned
+    against the series by the tests)."""
+    from .gamma import GAMMA
+    if min(dims) < 4:
+        raise ValueError("the closed form needs every extent >= 4")
+    mup = 2 * kappa * mu
+    one = np.eye(4)
+    a0i = (one - 1j * mup * GAMMA5) / (1 + mup * mup)
+    inner = a0i.copy()
+    for m in range(4):
+        pm, pp = one - GAMMA[m], one + GAMMA[m]
+        inner = inner + kappa ** 2 * (a0i @ pm @ a0i @ pp @ a0i + a0i @ pp @ a0i @ pm @ a0i)
+    c = np.array([3 * np.trace(INSERTIONS[g] @ inner) for g in range(16)])
+    return np.broadcast_to(c[:, None, None, None, None], (16,) + lattice.shape(dims)).copy()

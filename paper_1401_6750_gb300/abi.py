@@ -71,6 +71,8 @@ _SIGNATURES = {
     "tsm_make_diluted_sources": (c_int, [_P, c_uint64, c_uint64, c_int, c_int, c_int, _P, _P]),
     "tsm_contract_tdil": (c_int, [_P, c_int, _P, _P, c_int, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int),
                                   _P, c_int, _P]),
+    "tsm_contract_hpe": (c_int, [_P, c_double, c_double, c_int, _P, _P, c_int, ctypes.POINTER(c_int), c_int,
+                                 ctypes.POINTER(c_int), _P, c_int, _P]),
     "tsm_solve_sources": (c_int, [_P, c_double, c_double, c_int, c_double, c_int, c_uint64, c_uint64,
                                   c_int, c_int, _P, ctypes.POINTER(tsm_solve_stats), _P]),
     "tsm_solve_batch": (c_int, [ctypes.POINTER(tsm_batch_item), c_int, c_int, c_double, c_int, _P]),

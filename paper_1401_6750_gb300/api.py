@@ -161,6 +161,22 @@ class Gauge:
                                               int(accumulate), _stream(stream)), "tsm_contract_tdil")
         return out
 
+    def contract_hpe(self, kappa, mu, prec, native_s, native_eta, nsrc, t0, moms, out=None, accumulate=False,
+                     stream=None):
+        """contract_tdil with the hopping parameter expansion of the ultra-local insertions."""
+        moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        n_mom = moms.shape[0]
+        if out is None:
+            out = torch.zeros((abi.TSM_N_INSERTIONS, n_mom, self.dims[3], 2), dtype=torch.float64, device="cuda")
+        t0_c = None
+        if t0 is not None:
+            t0_a = np.ascontiguousarray(np.asarray(t0, dtype=np.int32))
+            t0_c = t0_a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        abi.check(abi.lib().tsm_contract_hpe(self.handle, kappa, mu, prec, _ptr(native_s), _ptr(native_eta), nsrc,
+                                             t0_c, n_mom, moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                             _ptr(out), int(accumulate), _stream(stream)), "tsm_contract_hpe")
+        return out
+
     def tsm(self, kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp_solver, hp_solver, noise_seed, moms, max_iter=100000,
             nrhs_per_launch=12, want_parts=False, stream=None):
         moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))

@@ -261,6 +261,17 @@ int tsm_contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta
                        pick_stream(g, stream));
 }
 
+int tsm_contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, const void* eta_dev,
+                     int nsrc, const int* t0_host, int n_mom, const int* mom, double* out_dev, int accumulate,
+                     void* stream) {
+  if (!g || !s_dev || !eta_dev || !out_dev || nsrc < 1 || nsrc > 65535 || n_mom < 1 || n_mom > 4096 || !mom)
+    return fail(TSM_ERR_INVALID_ARG, "tsm_contract_hpe: bad argument");
+  if (!isfinite(kappa) || !isfinite(mu) || kappa <= 0.0) return fail(TSM_ERR_INVALID_ARG, "bad kappa or mu");
+  TSM_TRY(bind(g));
+  return contract_hpe(g, kappa, mu, prec, s_dev, eta_dev, nsrc, t0_host, n_mom, mom, out_dev, accumulate,
+                      pick_stream(g, stream));
+}
+
 static int check_solver_args(const tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter) {
   if (!g) return fail(TSM_ERR_INVALID_ARG, "gauge is NULL");
   if (solver_kind(solver) < 0) return fail(TSM_ERR_INVALID_ARG, "bad solver %d", solver);

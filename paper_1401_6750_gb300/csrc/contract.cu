@@ -565,11 +565,133 @@ __global__ void __launch_bounds__(Z_BS) tdil_z_kernel(const double2* __restrict_
   }
 }
 
+// Hopping parameter expansion of the ultra-local insertions: their loops
+// come from the remainder field Y^4 s (A), plus the exact part of the first
+// four orders, a constant per site, added at p = 0 once per source covering
+// the timeslice (cnt[t] sources, Vs sites each); the derivative insertions
+// keep the plain loops (B).
+__global__ void hpe_merge_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                                 const double2* __restrict__ exact, const int* __restrict__ cnt, double vs, int m0,
+                                 int n_mom, int lt, double* out, int accumulate) {
+  const size_t n = (size_t)160 * n_mom * lt;
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int ins = (int)(k / ((size_t)n_mom * lt));
+  const int rem = (int)(k % ((size_t)n_mom * lt));
+  const int m = rem / lt, t = rem % lt;
+  double re, im;
+  if ((ins % 80) < 16) {
+    re = A[2 * k];
+    im = A[2 * k + 1];
+    if (m == m0) {
+      re += cnt[t] * vs * exact[ins].x;
+      im += cnt[t] * vs * exact[ins].y;
+    }
+  } else {
+    re = B[2 * k];
+    im = B[2 * k + 1];
+  }
+  if (accumulate) {
+    out[2 * k] += re;
+    out[2 * k + 1] += im;
+  } else {
+    out[2 * k] = re;
+    out[2 * k + 1] = im;
+  }
+}
+
+// Exact part of the hopping expansion per site for the 160 insertions (zero
+// for the derivative ones): with A0^-1 = (1 - i mu' g5)/(1 + mu'^2) and
+// P+-_mu = 1 +- g_mu, orders 0 and 2 (the only closed paths of length < 4
+// when every extent is >= 4: x -> x +- mu -> x, where U U^dag = 1) give
+//   c_u(Gamma) = 3 Tr_s[Gamma (A0^-1 + kappa^2 sum_mu (A0^-1 P- A0^-1 P+ A0^-1 + A0^-1 P+ A0^-1 P- A0^-1))]
+// and the d flavour conj(c_u(g5 Gamma^dag g5)).
+void hpe_exact(double kappa, double mu, HostCplx out[160]) {
+  Mat4 g[4], a0i, one, inner, t1, t2;
+  chiral_gammas(g);
+  const double mup = 2.0 * kappa * mu, d = 1.0 + mup * mup;
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      one[i][j] = HostCplx{i == j ? 1.0 : 0.0, 0.0};
+      a0i[i][j] = HostCplx{0.0, 0.0};
+    }
+  for (int i = 0; i < 4; ++i) a0i[i][i] = HostCplx{1.0 / d, (i < 2 ? -mup : mup) / d};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) inner[i][j] = a0i[i][j];
+  for (int m = 0; m < 4; ++m) {
+    Mat4 pm, pp;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        pm[i][j] = HostCplx{one[i][j].re - g[m][i][j].re, one[i][j].im - g[m][i][j].im};
+        pp[i][j] = HostCplx{one[i][j].re + g[m][i][j].re, one[i][j].im + g[m][i][j].im};
+      }
+    for (int order = 0; order < 2; ++order) {
+      const Mat4* first = order == 0 ? &pm : &pp;
+      const Mat4* second = order == 0 ? &pp : &pm;
+      mat_mul(a0i, *first, t1);
+      mat_mul(t1, a0i, t2);
+      mat_mul(t2, *second, t1);
+      mat_mul(t1, a0i, t2);
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          inner[i][j].re += kappa * kappa * t2[i][j].re;
+          inner[i][j].im += kappa * kappa * t2[i][j].im;
+        }
+    }
+  }
+  HostCplx cu[16];
+  Mat4 gam[16];
+  for (int idx = 0; idx < 16; ++idx) {
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) gam[idx][i][j] = one[i][j];
+    for (int bit = 0; bit < 4; ++bit)
+      if ((idx >> bit) & 1) {
+        mat_mul(gam[idx], g[bit], t1);
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j) gam[idx][i][j] = t1[i][j];
+      }
+    mat_mul(gam[idx], inner, t1);
+    double re = 0, im = 0;
+    for (int i = 0; i < 4; ++i) {
+      re += t1[i][i].re;
+      im += t1[i][i].im;
+    }
+    cu[idx] = HostCplx{3.0 * re, 3.0 * im};
+  }
+  for (int i = 0; i < 160; ++i) out[i] = HostCplx{0.0, 0.0};
+  for (int idx = 0; idx < 16; ++idx) {
+    // g5 Gamma^dag g5 = sign * Gamma_k
+    Mat4 gd;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const double s5 = ((i < 2) == (j < 2)) ? 1.0 : -1.0;
+        gd[i][j] = HostCplx{s5 * gam[idx][j][i].re, -s5 * gam[idx][j][i].im};
+      }
+    int kk = -1;
+    double sign = 0.0;
+    for (int k = 0; k < 16 && kk < 0; ++k)
+      for (double sg : {1.0, -1.0}) {
+        double diff = 0.0;
+        for (int i = 0; i < 4; ++i)
+          for (int j = 0; j < 4; ++j)
+            diff += fabs(gd[i][j].re - sg * gam[k][i][j].re) + fabs(gd[i][j].im - sg * gam[k][i][j].im);
+        if (diff < 1e-9) {
+          kk = k;
+          sign = sg;
+          break;
+        }
+      }
+    const HostCplx dd{sign * cu[kk].re, -sign * cu[kk].im};  // conj(sign c_u(k))
+    out[idx] = HostCplx{cu[idx].re - dd.re, cu[idx].im - dd.im};
+    out[80 + idx] = HostCplx{cu[idx].re + dd.re, cu[idx].im + dd.im};
+  }
+}
+
 }  // namespace
 
 struct ContractWorkspace {
   std::mutex mu;  // held for a whole contraction
-  DevBuf v, fields, part, mom, aux;
+  DevBuf v, fields, part, mom, aux, hpe;
 };
 
 void ContractWsDeleter::operator()(ContractWorkspace* w) const { delete w; }
@@ -710,20 +832,41 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
 }
 
 
-int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
-                  int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
+namespace {
+
+int contract_ws_slot(tsm_gauge* g, int slot, ContractWorkspace** out) {
+  std::lock_guard<std::mutex> lock(g->mu);
+  if (!g->contract_ws[slot]) g->contract_ws[slot].reset(new ContractWorkspace());
+  *out = g->contract_ws[slot].get();
+  if (!g->gamma_ready) {
+    GammaTable t;
+    TSM_TRY(build_gamma_table(t));
+    TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+    g->gamma_ready = true;
+  }
+  return TSM_OK;
+}
+
+int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, const void* eta_dev, int nsrc,
+              const std::vector<int>& t0, int rad, const std::vector<int>& mneg, int n_mom, const int* mom_host,
+              double* out_dev, int accumulate, cudaStream_t st);
+
+// argument checks shared by the standard-estimator entries: per-source
+// timeslices, momentum radius and the index of -p for every p
+int tdil_setup(const tsm_gauge* g, int prec, int nsrc, const int* t0_host, int n_mom, const int* mom_host,
+               std::vector<int>& t0, int& rad, std::vector<int>& mneg) {
   if (prec != TSM_F32 && prec != TSM_F64)
     return fail(TSM_ERR_INVALID_ARG, "contraction takes F32 or F64 fields, got precision %d", prec);
   if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
   const int lt = g->geom.L[3];
-  std::vector<int> t0(nsrc, -1);
+  t0.assign(nsrc, -1);
   if (t0_host)
     for (int r = 0; r < nsrc; ++r) {
       if (t0_host[r] < -1 || t0_host[r] >= lt) return fail(TSM_ERR_INVALID_ARG, "source %d: timeslice %d", r, t0_host[r]);
       t0[r] = t0_host[r];
     }
-  int rad = 0;
-  std::vector<int> mneg(n_mom);
+  rad = 0;
+  mneg.assign(n_mom, -1);
   for (int m = 0; m < n_mom; ++m) {
     for (int d = 0; d < 3; ++d) {
       const int n = mom_host[3 * m + d];
@@ -737,21 +880,29 @@ int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev
         mneg[m] = k;
     if (mneg[m] < 0) return fail(TSM_ERR_INVALID_ARG, "the momentum list must hold -p with every p");
   }
+  return TSM_OK;
+}
+
+}  // namespace
+
+int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
+                  int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
+  std::vector<int> t0, mneg;
+  int rad = 0;
+  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad, mneg));
   ContractWorkspace* wp;
-  {
-    std::lock_guard<std::mutex> lock(g->mu);
-    if (!g->contract_ws[0]) g->contract_ws[0].reset(new ContractWorkspace());
-    wp = g->contract_ws[0].get();
-    if (!g->gamma_ready) {
-      GammaTable t;
-      TSM_TRY(build_gamma_table(t));
-      TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
-      g->gamma_ready = true;
-    }
-  }
-  ContractWorkspace& w = *wp;
-  std::lock_guard<std::mutex> wlock(w.mu);
+  TSM_TRY(contract_ws_slot(g, 0, &wp));
+  std::lock_guard<std::mutex> wlock(wp->mu);
+  return tdil_body(g, *wp, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, out_dev, accumulate, st);
+}
+
+namespace {
+
+int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, const void* eta_dev, int nsrc,
+              const std::vector<int>& t0, int rad, const std::vector<int>& mneg, int n_mom, const int* mom_host,
+              double* out_dev, int accumulate, cudaStream_t st) {
   const int V = g->geom.V;
+  const int lt = g->geom.L[3];
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2];
   const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
@@ -784,6 +935,66 @@ int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev
                                                    rad, out_dev, accumulate);
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
+}
+
+}  // namespace
+
+int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, const void* eta_dev, int nsrc,
+                 const int* t0_host, int n_mom, const int* mom_host, double* out_dev, int accumulate,
+                 cudaStream_t st) {
+  for (int d = 0; d < 4; ++d)
+    if (g->geom.L[d] < 4) return fail(TSM_ERR_INVALID_ARG, "the expansion's exact part needs every extent >= 4");
+  std::vector<int> t0, mneg;
+  int rad = 0;
+  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad, mneg));
+  const int lt = g->geom.L[3];
+  int m0 = -1;
+  for (int m = 0; m < n_mom; ++m)
+    if (mom_host[3 * m] == 0 && mom_host[3 * m + 1] == 0 && mom_host[3 * m + 2] == 0) m0 = m;
+  std::vector<int> cnt(lt, 0);
+  for (int r = 0; r < nsrc; ++r) {
+    if (t0[r] < 0)
+      for (int t = 0; t < lt; ++t) ++cnt[t];
+    else
+      ++cnt[t0[r]];
+  }
+  HostCplx ex[160];
+  hpe_exact(kappa, mu, ex);
+  ContractWorkspace* wp;
+  TSM_TRY(contract_ws_slot(g, 0, &wp));
+  ContractWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
+  const size_t fs = (size_t)nsrc * spinor_chunks(prec) * g->geom.V * 16;
+  const size_t n_out = (size_t)160 * n_mom * lt * 2;
+  const size_t bytes = 2 * fs + 2 * n_out * sizeof(double) + 160 * sizeof(double2) + (size_t)lt * sizeof(int);
+  TSM_TRY(w.hpe.reserve(bytes));
+  char* base = w.hpe.as<char>();
+  void* ya = base;
+  void* yb = base + fs;
+  double* tmp_a = reinterpret_cast<double*>(base + 2 * fs);
+  double* tmp_b = tmp_a + n_out;
+  double2* ex_dev = reinterpret_cast<double2*>(tmp_b + n_out);
+  int* cnt_dev = reinterpret_cast<int*>(ex_dev + 160);
+  // Y = A0^-1 kappa H = (h0 + i h1 g5) H,  h0 + i h1 g5 = kappa (1 - i mu' g5) / (1 + mu'^2)
+  const double mup = 2.0 * kappa * mu, dd = 1.0 + mup * mup;
+  const double h0 = kappa / dd, h1 = -kappa * mup / dd;
+  TSM_TRY(hop_general(g, prec, s_dev, nullptr, ya, nsrc, 0.0, 0.0, h0, h1, st));
+  TSM_TRY(hop_general(g, prec, ya, nullptr, yb, nsrc, 0.0, 0.0, h0, h1, st));
+  TSM_TRY(hop_general(g, prec, yb, nullptr, ya, nsrc, 0.0, 0.0, h0, h1, st));
+  TSM_TRY(hop_general(g, prec, ya, nullptr, yb, nsrc, 0.0, 0.0, h0, h1, st));
+  TSM_TRY(tdil_body(g, w, prec, yb, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, tmp_a, 0, st));
+  TSM_TRY(tdil_body(g, w, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, tmp_b, 0, st));
+  std::vector<double2> exh(160);
+  for (int i = 0; i < 160; ++i) exh[i] = make_double2(ex[i].re, ex[i].im);
+  TSM_CUDA(cudaMemcpyAsync(ex_dev, exh.data(), sizeof(double2) * 160, cudaMemcpyHostToDevice, st));
+  TSM_CUDA(cudaMemcpyAsync(cnt_dev, cnt.data(), sizeof(int) * lt, cudaMemcpyHostToDevice, st));
+  const double vs = (double)g->geom.L[0] * g->geom.L[1] * g->geom.L[2];
+  const size_t n = (size_t)160 * n_mom * lt;
+  count_launches(1);
+  hpe_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp_a, tmp_b, ex_dev, cnt_dev, vs, m0, n_mom, lt,
+                                                                 out_dev, accumulate);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;  // pageable sources of the copies above are staged before the calls return
 }
 }  // namespace tsm
 

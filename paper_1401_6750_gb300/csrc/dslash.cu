@@ -158,6 +158,38 @@ int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, 
   return fail(TSM_ERR_INVALID_ARG, "fixed-shape launch supports F64 and F32 fields");
 }
 
+int hop_general(tsm_gauge* g, int prec, const void* in, const void* center, void* out, int nrhs, double c0,
+                double c1, double h0, double h1, cudaStream_t s) {
+  if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
+  auto setup = [&](DslashArgs& a) {
+    a.g = g->geom;
+    a.links = g->links[prec].p;
+    a.in = in;
+    a.nblk = (g->geom.V + DSLASH_BS - 1) / DSLASH_BS;
+    a.nrhs = nrhs;
+    set_coeffs(a, 0.0, 0.0);
+    set_eo(a, center, 0, c0, c1, h0, h1);
+    a.general = 1;
+  };
+  const size_t V = (size_t)g->geom.V;
+  count_launches(1);
+  if (prec == TSM_F64) {
+    DslashArgs a;
+    setup(a);
+    EpiStore<double, TSM_F64> e{out, V, 0, RedSlots{nullptr, nullptr}};
+    launch_dslash<double, -1, TSM_F64, TSM_F64>(1, a, e, s);
+  } else if (prec == TSM_F32) {
+    DslashArgs a;
+    setup(a);
+    EpiStore<float, TSM_F32> e{out, V, 0, RedSlots{nullptr, nullptr}};
+    launch_dslash<float, -1, TSM_F32, TSM_F32>(1, a, e, s);
+  } else {
+    return fail(TSM_ERR_INVALID_ARG, "general hop on F64 or F32 fields only");
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
 int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
                  cudaStream_t s) {
   return dslash_apply_mixed(g, prec, prec, op, kappa, mu, in, out, nrhs, 0, s);

@@ -58,11 +58,13 @@ struct DslashArgs {
   // checkerboarded operator (even-odd kernels only):
   //   out(j) = (c0 + i c1 g5) center(j) + (h0 + i h1 g5) hop(in)(j)
   // on the sites of parity `parity`, j = full site >> 1; center may be null.
-  const void* center;
-  int parity;
-  double c0, c1, h0, h1;
-  float c0_f, c1_f, h0_f, h1_f;
-  dsf c0_ds, c1_ds, h0_ds, h1_ds;
+  const void* center = nullptr;
+  int parity = 0;
+  double c0 = 0, c1 = 0, h0 = 0, h1 = 0;
+  float c0_f = 0, c1_f = 0, h0_f = 0, h1_f = 0;
+  dsf c0_ds{0.0f, 0.0f}, c1_ds{0.0f, 0.0f}, h0_ds{0.0f, 0.0f}, h1_ds{0.0f, 0.0f};
+  // full-volume kernels: general = 1 replaces M by the coefficient form above
+  int general = 0;
 };
 
 __host__ __device__ inline void set_eo(DslashArgs& a, const void* center, int parity, double c0, double c1, double h0,
@@ -427,6 +429,28 @@ __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashA
     stencil_dir<1, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
     stencil_dir<2, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
     stencil_dir<3, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
+  }
+  if (a.general) {  // (c0 + i c1 g5) centre + (h0 + i h1 g5) hop
+    R c0, c1, h0, h1;
+    EoCoef<R>::get(a, c0, c1, h0, h1);
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) continue;
+      cplx<R> ctr[12];
+      if (a.center) {
+        SpinorIO<PIN>::load(a.center, (size_t)a.g.V, r0 + j, i, ctr);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ctr[k] = mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const R g5 = (k < 6) ? (R)1 : (R)-1;
+        const cplx<R> hv = out[j][k];
+        out[j][k] = c0 * ctr[k] + (g5 * c1) * times_i(ctr[k]) + h0 * hv + (g5 * h1) * times_i(hv);
+      }
+    }
+    return;
   }
   const R kap = arg_kappa<R>(a), tw = arg_tw<R>(a);
 #pragma unroll

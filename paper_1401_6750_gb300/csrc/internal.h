@@ -137,6 +137,10 @@ int dslash_apply(tsm_gauge* g, int prec, int op, double kappa, double mu, const 
 // the combinations instantiated there); gamma5 != 0 stores g5 * result.
 int dslash_apply_mixed(tsm_gauge* g, int prec_field, int prec_links, int op, double kappa, double mu,
                        const void* in, void* out, int nrhs, int gamma5, cudaStream_t s);
+// out = (c0 + i c1 g5) center + (h0 + i h1 g5) H in on full-volume F64/F32 fields (center may be null),
+// H the hopping term of M = A0 - kappa H
+int hop_general(tsm_gauge* g, int prec, const void* in, const void* center, void* out, int nrhs, double c0,
+                double c1, double h0, double h1, cudaStream_t s);
 // M or A on F64/F32 fields with a fixed number of right-hand sides per thread (no autotuning, no allocation).
 int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, const void* in, void* out, int nrhs,
                        int gamma5, int nr, cudaStream_t s);
@@ -192,6 +196,10 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
 // sources: t0[r] = -1) and their solutions s (contract.cu)
 int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
                   int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
+// Standard-estimator loops with the hopping parameter expansion of the 16
+// ultra-local insertions (both flavours); derivative insertions plain
+int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, const void* eta_dev, int nsrc,
+                 const int* t0_host, int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                            const int* mom_host, double* out_dev, int accumulate, cudaStream_t s);
 

@@ -60,6 +60,7 @@ def test_exact_part_closed_form(t_bc):
     for g in range(16):
         want = 3 * np.trace(INSERTIONS[g] @ inner)
         assert np.max(np.abs(ex[g] - want)) < 1e-12, g
+    assert np.max(np.abs(hpe.exact_ultralocal_constant(dims, kappa, mu) - ex)) < 1e-12
 
 
 def test_remainder_suppression():
