@@ -425,6 +425,40 @@ def hpe_variance(g, abi, torch, w, lp_solver, n=16):
             "note": "variances per source of the p = 0 loops summed over timeslices"}
 
 
+def binary_storage(g, abi, torch, w, lp_solver, moms, nrhs, k_end=5):
+    """Binary-weight accumulation (Sec. 2.1.1, Fig. 2) of the bulk LP loops of
+    2^k_end - 1 sources into block files in a temporary directory: wall time,
+    files and bytes against one file per source, and the any-N read back."""
+    import shutil
+    import tempfile
+    from paper_1401_6750_gb300 import api
+    T = g.dims[3]
+    n_values = 160 * len(moms) * T * 2
+    d = tempfile.mkdtemp(prefix="tsm_blocks_")
+    try:
+        st = api.BinStore(os.path.join(d, "bulk"), n_values)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        stats = st.accumulate(g, w["kappa"], w["mu"], lp_solver, w["rho_lp"], 2025, moms, k_end,
+                              nrhs_per_launch=nrhs)
+        t_acc = time.perf_counter() - t0
+        n = st.sources
+        t0 = time.perf_counter()
+        for m in (n, n // 2 + 1):
+            st.mean(m)
+        t_read = (time.perf_counter() - t0) / 2
+        files = sorted(f for f in os.listdir(d) if f.endswith(".bin"))
+        size = sum(os.path.getsize(os.path.join(d, f)) for f in files)
+        st.close()
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    per_source = n_values * 8
+    return {"sources": n, "files": len(files), "bytes": size, "bytes_one_file_per_source": n * per_source,
+            "storage_reduction": 1.0 - size / (n * per_source), "seconds_accumulate": t_acc,
+            "sources_per_s": n / t_acc, "seconds_mean_any_n": t_read,
+            "lp_iterations_mean": stats["lp_iterations_total"] / n}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -572,9 +606,11 @@ def main():
 
     tdil = None
     hpe_var = None
+    binstore = None
     if rank == 0 and not args.no_tdil:
         tdil = time_dilution(g, abi, torch, w, lp_solver, moms)
         hpe_var = hpe_variance(g, abi, torch, w, lp_solver)
+        binstore = binary_storage(g, abi, torch, w, lp_solver, moms, args.nrhs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -605,6 +641,7 @@ def main():
             "equal_accuracy": eq,
             "time_dilution": tdil,
             "hpe": hpe_var,
+            "binary_storage": binstore,
         }
         print(json.dumps(line), flush=True)
     g.close()

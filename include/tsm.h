@@ -342,6 +342,40 @@ int tsm_solve_tsm_dev(tsm_gauge* g, const tsm_params* p, double* loops_dev,
 
 /* ---------------------------------------------------------------- helpers */
 
+/* Binary-weight storage of loop sums (Sec. 2.1.1, Fig. 2).  The file of
+ * weight 2^k, "<path_prefix>.w<2^k>.bin", holds the sum of the contractions
+ * of the 2^k sources 2^k - 1 .. 2^{k+1} - 2 (0-based ids; the paper's
+ * File.1, File.2, File.4 ... counting from 1), n_values doubles after a
+ * header with an FNV-1a checksum.  Any N sources are recovered from the files
+ * of N's set bits, so N sources take log2 N files.  Host-only calls (no GPU
+ * use) except tsm_accumulate_blocks.
+ *   tsm_binstore_open   opens (the directory must exist) and validates every
+ *                       block file present; TSM_ERR_INVALID_ARG on a corrupt,
+ *                       truncated or mismatched file.  Free with _close.
+ *   tsm_binstore_sources  2^K - 1 for the contiguous blocks 0..K-1 present:
+ *                       where an interrupted accumulation resumes.
+ *   tsm_binstore_block  the source range of block k.
+ *   tsm_binstore_put    writes block k (written to a temporary name, then
+ *                       renamed into place).
+ *   tsm_binstore_mean   out = (sum of the blocks of n's bits) / n; fails if
+ *                       one of them is missing.
+ *   tsm_accumulate_blocks  computes the bulk LP loops (p's lp_solver, rho_lp,
+ *                       kappa, mu, noise_seed, max_iter, nrhs_per_launch,
+ *                       momenta; one-end contraction as tsm_solve_tsm) of
+ *                       every block from the first one missing up to
+ *                       k_end - 1 and stores them; the store's n_values must
+ *                       be 160 * n_mom * T * 2.  stats: LP fields only. */
+typedef struct tsm_binstore tsm_binstore;
+int tsm_binstore_open(const char* path_prefix, size_t n_values,
+                      tsm_binstore** out);
+void tsm_binstore_close(tsm_binstore* st);
+long long tsm_binstore_sources(const tsm_binstore* st);
+int tsm_binstore_block(int k, long long* first_source, long long* n_sources);
+int tsm_binstore_put(tsm_binstore* st, int k, const double* block_sum_host);
+int tsm_binstore_mean(const tsm_binstore* st, long long n, double* out_host);
+int tsm_accumulate_blocks(tsm_gauge* g, const tsm_params* p, tsm_binstore* st,
+                          int k_end, tsm_stats* stats, void* stream);
+
 /* Momenta n with n^2 <= p2max, ordered by n^2 then lexicographically
  * (Sec. 2.3 cut on p^2); writes min(count, cap) triples, returns the count
  * (123 for p2max = 9), or -1 if p2max < 0. */

@@ -73,6 +73,13 @@ _SIGNATURES = {
                                   _P, c_int, _P]),
     "tsm_contract_hpe": (c_int, [_P, c_double, c_double, c_int, _P, _P, c_int, ctypes.POINTER(c_int), c_int,
                                  ctypes.POINTER(c_int), _P, c_int, _P]),
+    "tsm_binstore_open": (c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(c_void_p)]),
+    "tsm_binstore_close": (None, [_P]),
+    "tsm_binstore_sources": (ctypes.c_longlong, [_P]),
+    "tsm_binstore_block": (c_int, [c_int, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+    "tsm_binstore_put": (c_int, [_P, c_int, ctypes.POINTER(c_double)]),
+    "tsm_binstore_mean": (c_int, [_P, ctypes.c_longlong, ctypes.POINTER(c_double)]),
+    "tsm_accumulate_blocks": (c_int, [_P, ctypes.POINTER(tsm_params), _P, c_int, ctypes.POINTER(tsm_stats), _P]),
     "tsm_solve_sources": (c_int, [_P, c_double, c_double, c_int, c_double, c_int, c_uint64, c_uint64,
                                   c_int, c_int, _P, ctypes.POINTER(tsm_solve_stats), _P]),
     "tsm_solve_batch": (c_int, [ctypes.POINTER(tsm_batch_item), c_int, c_int, c_double, c_int, _P]),

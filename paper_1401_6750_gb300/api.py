@@ -279,3 +279,54 @@ class OneEndLoops(torch.autograd.Function):
 def one_end_loops(mu, eta, gauge, kappa, moms, solver=abi.TSM_SOLVER_F64, rho=1e-12, prec=abi.TSM_F64,
                   max_iter=100000):
     return OneEndLoops.apply(mu, eta, gauge, kappa, moms, solver, rho, prec, max_iter)
+
+
+class BinStore:
+    """Binary-weight storage of loop sums (block k: sources 2^k - 1 ..
+    2^{k+1} - 2, any N from its bits).  Host-side; `accumulate` fills it on
+    the GPU with the bulk LP loops."""
+
+    def __init__(self, path_prefix, n_values):
+        self.n_values = int(n_values)
+        h = ctypes.c_void_p()
+        abi.check(abi.lib().tsm_binstore_open(str(path_prefix).encode(), self.n_values, ctypes.byref(h)),
+                  "tsm_binstore_open")
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            abi.lib().tsm_binstore_close(self.handle)
+            self.handle = None
+
+    @property
+    def sources(self):
+        return int(abi.lib().tsm_binstore_sources(self.handle))
+
+    @staticmethod
+    def block(k):
+        first, count = ctypes.c_longlong(), ctypes.c_longlong()
+        abi.check(abi.lib().tsm_binstore_block(k, ctypes.byref(first), ctypes.byref(count)), "tsm_binstore_block")
+        return first.value, count.value
+
+    def put(self, k, block_sum):
+        a = np.ascontiguousarray(np.asarray(block_sum, dtype=np.float64).ravel())
+        if a.size != self.n_values:
+            raise ValueError("block holds %d values, store expects %d" % (a.size, self.n_values))
+        abi.check(abi.lib().tsm_binstore_put(self.handle, k, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                  "tsm_binstore_put")
+
+    def mean(self, n):
+        out = np.empty(self.n_values, dtype=np.float64)
+        abi.check(abi.lib().tsm_binstore_mean(self.handle, n, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                  "tsm_binstore_mean")
+        return out
+
+    def accumulate(self, gauge, kappa, mu, lp_solver, rho_lp, noise_seed, moms, k_end, max_iter=100000,
+                   nrhs_per_launch=32, stream=None):
+        moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32).reshape(-1, 3))
+        p = abi.tsm_params(kappa, mu, 0, 0, rho_lp, 0.5, lp_solver, lp_solver, noise_seed, max_iter,
+                           nrhs_per_launch, moms.shape[0], moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        st = abi.tsm_stats()
+        abi.check(abi.lib().tsm_accumulate_blocks(gauge.handle, ctypes.byref(p), self.handle, k_end,
+                                                  ctypes.byref(st), _stream(stream)), "tsm_accumulate_blocks")
+        return dict((f, getattr(st, f)) for f, _ in st._fields_)
