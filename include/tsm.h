@@ -155,6 +155,18 @@ int tsm_dslash_tm(tsm_gauge* g, double kappa, double mu, int op, int prec,
 int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src,
                      int nsrc, int prec, void* out_dev, void* stream);
 
+/* Synthetic gauge field on the host (no GPU use): U_mu(x) = exp(i eps H),
+ * H = sum_a h_a lambda_a / 2 with h_a ~ N(0, 1) and lambda_a the Gell-Mann
+ * matrices, the stand-in for the paper's ensembles.  The eight normals of
+ * link (site i, direction mu) are Box-Muller pairs of the eight 32-bit
+ * halves (low half first, u = (w + 1/2) / 2^32) of the words of
+ * Philox4x64-10(counter = {4 i + mu, 0, 0, 0}, key = {seed, 0x67617567});
+ * the exponential goes through the eigenvectors of H (Jacobi rotations), in
+ * FP64.  links_out: [V][4][3][3] complex as 18 doubles per link, row-major,
+ * site i = x + Lx*(y + Ly*(z + Lz*t)) -- the layout tsm_create_gauge takes. */
+int tsm_generate_gauge_host(const int dims[4], double eps, uint64_t seed,
+                            double* links_out);
+
 /* Time dilution (Sec. 2.2): n_t fields, field k being the Z4 source of
  * (noise_seed, source_id) -- the same values tsm_make_sources gives for
  * first_src = source_id -- kept on timeslice t_first + k and zero on every

@@ -73,6 +73,7 @@ _SIGNATURES = {
                                   _P, c_int, _P]),
     "tsm_contract_hpe": (c_int, [_P, c_double, c_double, c_int, _P, _P, c_int, ctypes.POINTER(c_int), c_int,
                                  ctypes.POINTER(c_int), _P, c_int, _P]),
+    "tsm_generate_gauge_host": (c_int, [ctypes.POINTER(c_int), c_double, c_uint64, ctypes.POINTER(c_double)]),
     "tsm_binstore_open": (c_int, [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(c_void_p)]),
     "tsm_binstore_close": (None, [_P]),
     "tsm_binstore_sources": (ctypes.c_longlong, [_P]),

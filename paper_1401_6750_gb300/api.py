@@ -330,3 +330,14 @@ class BinStore:
         abi.check(abi.lib().tsm_accumulate_blocks(gauge.handle, ctypes.byref(p), self.handle, k_end,
                                                   ctypes.byref(st), _stream(stream)), "tsm_accumulate_blocks")
         return dict((f, getattr(st, f)) for f, _ in st._fields_)
+
+
+def generate_gauge_host(dims, eps, seed):
+    """The library's host generator of U = exp(i eps H) links (see
+    tsm_generate_gauge_host): complex128 (T, Lz, Ly, Lx, 4, 3, 3)."""
+    lx, ly, lz, lt = dims
+    out = np.empty((lt, lz, ly, lx, 4, 3, 3, 2), dtype=np.float64)
+    d = (ctypes.c_int * 4)(*dims)
+    abi.check(abi.lib().tsm_generate_gauge_host(d, eps, seed, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+              "tsm_generate_gauge_host")
+    return out[..., 0] + 1j * out[..., 1]

@@ -241,6 +241,13 @@ int tsm_make_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t first_src, int 
   return make_sources(g, noise_seed, first_src, nsrc, prec, out_dev, pick_stream(g, stream));
 }
 
+int tsm_generate_gauge_host(const int dims[4], double eps, uint64_t seed, double* links_out) {
+  if (!dims || !links_out || !isfinite(eps)) return fail(TSM_ERR_INVALID_ARG, "tsm_generate_gauge_host: bad argument");
+  for (int d = 0; d < 4; ++d)
+    if (dims[d] < 1) return fail(TSM_ERR_INVALID_ARG, "extent %d is %d", d, dims[d]);
+  return generate_gauge_host(dims, eps, seed, links_out);
+}
+
 int tsm_make_diluted_sources(tsm_gauge* g, uint64_t noise_seed, uint64_t source_id, int t_first, int n_t, int prec,
                              void* out_dev, void* stream) {
   if (!g || !out_dev || !valid_prec(prec) || n_t < 0 || n_t > 65535 || t_first < 0 ||

@@ -64,7 +64,15 @@ __global__ void pack_links_16(const double2* __restrict__ src, uint4* __restrict
 // ------------------------------------------------------------------ Philox4x64-10
 // Salmon, Moraes, Dror, Shaw, SC'11: round (X0..X3) -> (hi(M1 X2) ^ X1 ^ K0,
 // lo(M1 X2), hi(M0 X0) ^ X3 ^ K1, lo(M0 X0)); key += Weyl constants between rounds.
-__device__ __forceinline__ void philox4x64_10(uint64_t (&x)[4], uint64_t k0, uint64_t k1) {
+__host__ __device__ __forceinline__ uint64_t mulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+__host__ __device__ __forceinline__ void philox4x64_10(uint64_t (&x)[4], uint64_t k0, uint64_t k1) {
   const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
   const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
 #pragma unroll
@@ -73,8 +81,8 @@ __device__ __forceinline__ void philox4x64_10(uint64_t (&x)[4], uint64_t k0, uin
       k0 += W0;
       k1 += W1;
     }
-    const uint64_t lo0 = M0 * x[0], hi0 = __umul64hi(M0, x[0]);
-    const uint64_t lo1 = M1 * x[2], hi1 = __umul64hi(M1, x[2]);
+    const uint64_t lo0 = M0 * x[0], hi0 = mulhi64(M0, x[0]);
+    const uint64_t lo1 = M1 * x[2], hi1 = mulhi64(M1, x[2]);
     const uint64_t n0 = hi1 ^ x[1] ^ k0, n2 = hi0 ^ x[3] ^ k1;
     x[0] = n0;
     x[1] = lo1;
@@ -195,6 +203,111 @@ int build_links(tsm_gauge* g, const double* links_host) {
     TSM_CUDA(cudaGetLastError());
   }
   TSM_CUDA(cudaDeviceSynchronize());
+  return TSM_OK;
+}
+
+// ------------------------------------------------------------------ host gauge generator
+// U = exp(i eps H), H = sum_a h_a lambda_a / 2 with h_a ~ N(0, 1): the eight
+// normals of link (site i, direction mu) come from one Philox4x64-10 call
+// (counter {4 i + mu, 0, 0, 0}, key {seed, 0x67617567}), its four words split
+// into eight 32-bit uniforms u = (w + 1/2) / 2^32 and paired by Box-Muller.
+// The exponential goes through the eigenvectors of H from cyclic Jacobi
+// rotations (Golub and Van Loan, 8.5), in FP64.
+namespace {
+
+struct HC {
+  double re, im;
+};
+inline HC hmul(HC a, HC b) { return HC{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline HC hconj(HC a) { return HC{a.re, -a.im}; }
+inline HC hadd(HC a, HC b) { return HC{a.re + b.re, a.im + b.im}; }
+inline HC hscale(HC a, double s) { return HC{a.re * s, a.im * s}; }
+
+// Eigen-decomposition of a Hermitian 3x3 a = v diag(w) v^dag by cyclic Jacobi.
+void jacobi_herm3(HC a[3][3], double w[3], HC v[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) v[i][j] = HC{i == j ? 1.0 : 0.0, 0.0};
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 3; ++q) off += a[p][q].re * a[p][q].re + a[p][q].im * a[p][q].im;
+    if (off < 1e-34) break;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        const double mag = sqrt(a[p][q].re * a[p][q].re + a[p][q].im * a[p][q].im);
+        if (mag < 1e-300) continue;
+        // phase that makes a[p][q] real, then a real symmetric 2x2 rotation
+        const HC ph = HC{a[p][q].re / mag, a[p][q].im / mag};
+        const double theta = 0.5 * (a[q][q].re - a[p][p].re) / mag;
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        // J: columns p, q of the identity mixed: J[p][p] = c, J[q][q] = c,
+        // J[p][q] = s ph, J[q][p] = -s conj(ph); a <- J^dag a J, v <- v J
+        HC jpp{c, 0.0}, jqq{c, 0.0}, jpq = hscale(ph, s), jqp = hscale(hconj(ph), -s);
+        for (int k = 0; k < 3; ++k) {  // a <- a J (columns p, q)
+          const HC akp = a[k][p], akq = a[k][q];
+          a[k][p] = hadd(hmul(akp, jpp), hmul(akq, jqp));
+          a[k][q] = hadd(hmul(akp, jpq), hmul(akq, jqq));
+          const HC vkp = v[k][p], vkq = v[k][q];
+          v[k][p] = hadd(hmul(vkp, jpp), hmul(vkq, jqp));
+          v[k][q] = hadd(hmul(vkp, jpq), hmul(vkq, jqq));
+        }
+        for (int k = 0; k < 3; ++k) {  // a <- J^dag a (rows p, q)
+          const HC apk = a[p][k], aqk = a[q][k];
+          a[p][k] = hadd(hmul(hconj(jpp), apk), hmul(hconj(jqp), aqk));
+          a[q][k] = hadd(hmul(hconj(jpq), apk), hmul(hconj(jqq), aqk));
+        }
+      }
+  }
+  for (int i = 0; i < 3; ++i) w[i] = a[i][i].re;
+}
+
+}  // namespace
+
+int generate_gauge_host(const int dims[4], double eps, uint64_t seed, double* out) {
+  const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  static const double kPi = 3.14159265358979323846;
+  for (long long i = 0; i < V; ++i)
+    for (int mu = 0; mu < 4; ++mu) {
+      uint64_t x[4] = {(uint64_t)(4 * i + mu), 0ull, 0ull, 0ull};
+      philox4x64_10(x, seed, 0x67617567ull);
+      double u[8], h[8];
+      for (int k = 0; k < 4; ++k) {
+        u[2 * k] = ((double)(uint32_t)(x[k] & 0xffffffffu) + 0.5) * 0x1p-32;
+        u[2 * k + 1] = ((double)(uint32_t)(x[k] >> 32) + 0.5) * 0x1p-32;
+      }
+      for (int k = 0; k < 4; ++k) {
+        const double r = sqrt(-2.0 * log(u[2 * k])), ph = 2.0 * kPi * u[2 * k + 1];
+        h[2 * k] = r * cos(ph);
+        h[2 * k + 1] = r * sin(ph);
+      }
+      // H = sum_a h_a lambda_a / 2 (Gell-Mann basis)
+      const double r3 = 1.0 / sqrt(3.0);
+      HC a[3][3];
+      a[0][0] = HC{0.5 * (h[2] + h[7] * r3), 0.0};
+      a[1][1] = HC{0.5 * (-h[2] + h[7] * r3), 0.0};
+      a[2][2] = HC{0.5 * (-2.0 * h[7] * r3), 0.0};
+      a[0][1] = HC{0.5 * h[0], -0.5 * h[1]};
+      a[0][2] = HC{0.5 * h[3], -0.5 * h[4]};
+      a[1][2] = HC{0.5 * h[5], -0.5 * h[6]};
+      a[1][0] = hconj(a[0][1]);
+      a[2][0] = hconj(a[0][2]);
+      a[2][1] = hconj(a[1][2]);
+      double w[3];
+      HC v[3][3];
+      jacobi_herm3(a, w, v);
+      double* o = out + ((size_t)i * 4 + mu) * 18;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          HC sum{0.0, 0.0};
+          for (int k = 0; k < 3; ++k) {
+            const HC e{cos(eps * w[k]), sin(eps * w[k])};
+            sum = hadd(sum, hmul(hmul(v[r][k], e), hconj(v[c][k])));
+          }
+          o[2 * (3 * r + c)] = sum.re;
+          o[2 * (3 * r + c) + 1] = sum.im;
+        }
+    }
   return TSM_OK;
 }
 

@@ -159,6 +159,9 @@ int spinor_convert(const tsm_gauge* g, int prec_dst, void* dst, int prec_src, co
                    int gamma5, cudaStream_t s);
 int build_links(tsm_gauge* g, const double* links_host);
 
+// Host synthetic gauge field U = exp(i eps H) (fields.cu; host only)
+int generate_gauge_host(const int dims[4], double eps, uint64_t seed, double* out);
+
 // ---- solver (solver.cu)
 // Solve M(mu) x = eta for nrhs right-hand sides.  eta (device, native layout of
 // eta_prec) or, when eta is null, the Z4 sources (seed, first .. first+nrhs-1).
