@@ -217,6 +217,162 @@ __global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) contract_field
   }
 }
 
+// The same site fields with FP32 sums in packed pairs (two-wide FP32 FMA):
+// a spinor is held as pairs over adjacent spins, re[c][h] = (x[6h + c].re,
+// x[6h + 3 + c].re) for spins (2h, 2h + 1), and a 4x4 Dirac matrix as pairs
+// over adjacent columns, re[a][h] = (m[a][2h].re, m[a][2h + 1].re).
+struct SpinP {
+  float2 re[3][2], im[3][2];
+};
+struct Mat4P {
+  float2 re[4][2], im[4][2];
+};
+
+__device__ __forceinline__ float2 bc2f(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ void pack_spin(SpinP& p, const cplx<float> (&x)[12]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      p.re[c][h] = make_float2(x[6 * h + c].re, x[6 * h + 3 + c].re);
+      p.im[c][h] = make_float2(x[6 * h + c].im, x[6 * h + 3 + c].im);
+    }
+}
+// component (spin a, colour c) of either form
+__device__ __forceinline__ cplx<float> comp(const cplx<float> (&x)[12], int a, int c) { return x[3 * a + c]; }
+__device__ __forceinline__ cplx<float> comp(const SpinP& x, int a, int c) {
+  const float2 r = x.re[c][a >> 1], i = x.im[c][a >> 1];
+  return (a & 1) ? mk<float>(r.y, i.y) : mk<float>(r.x, i.x);
+}
+
+// w = U p for all four spins (pairs over spins)
+__device__ __forceinline__ void matvec_p(SpinP& w, const cplx<float> (&u)[3][3], const SpinP& p) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float2 wr = __fmul2_rn(bc2f(u[a][0].re), p.re[0][h]);
+      float2 wi = __fmul2_rn(bc2f(u[a][0].re), p.im[0][h]);
+      wr = __ffma2_rn(bc2f(-u[a][0].im), p.im[0][h], wr);
+      wi = __ffma2_rn(bc2f(u[a][0].im), p.re[0][h], wi);
+#pragma unroll
+      for (int b = 1; b < 3; ++b) {
+        wr = __ffma2_rn(bc2f(u[a][b].re), p.re[b][h], wr);
+        wr = __ffma2_rn(bc2f(-u[a][b].im), p.im[b][h], wr);
+        wi = __ffma2_rn(bc2f(u[a][b].re), p.im[b][h], wi);
+        wi = __ffma2_rn(bc2f(u[a][b].im), p.re[b][h], wi);
+      }
+      w.re[a][h] = wr;
+      w.im[a][h] = wi;
+    }
+}
+
+// m[a][b] += sum_c conj(l_ac) r_bc   (times -1 when SUB); r in pairs over spins b
+template <bool SUB, class L>
+__device__ __forceinline__ void outer_p(Mat4P& m, const L& l, const SpinP& r) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const cplx<float> x = comp(l, a, c);
+      const float lr = SUB ? -x.re : x.re, li = SUB ? -x.im : x.im;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        m.re[a][h] = __ffma2_rn(bc2f(lr), r.re[c][h], m.re[a][h]);
+        m.re[a][h] = __ffma2_rn(bc2f(li), r.im[c][h], m.re[a][h]);
+        m.im[a][h] = __ffma2_rn(bc2f(lr), r.im[c][h], m.im[a][h]);
+        m.im[a][h] = __ffma2_rn(bc2f(-li), r.re[c][h], m.im[a][h]);
+      }
+    }
+}
+
+__device__ __forceinline__ void unpack_mat(cplx<float> (&m)[16], const Mat4P& p) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      m[4 * a + 2 * h] = mk<float>(p.re[a][h].x, p.im[a][h].x);
+      m[4 * a + 2 * h + 1] = mk<float>(p.re[a][h].y, p.im[a][h].y);
+    }
+}
+
+template <int PS, int PL>
+__global__ void __launch_bounds__(FLD_BS, 3) contract_fields_pairs_kernel(FieldArgs<float> a) {
+  const int pass = blockIdx.x % 5;
+  const int i = (blockIdx.x / 5) * FLD_BS + threadIdx.x;
+  if (i >= a.g.V) return;
+  const size_t V = (size_t)a.g.V;
+  Mat4P p0, p1;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) p0.re[x][h] = p0.im[x][h] = p1.re[x][h] = p1.im[x][h] = make_float2(0.0f, 0.0f);
+  float scale = 1.0f;
+  if (pass == 0) {
+    for (int r = 0; r < a.nsrc; ++r) {
+      cplx<float> s0[12], v0[12];
+      SpinorIO<PS>::load(a.s, V, r, i, s0);
+      SpinorIO<PS>::load(a.v, V, r, i, v0);
+      SpinP sp, vp;
+      pack_spin(sp, s0);
+      pack_spin(vp, v0);
+      outer_p<false>(p0, s0, sp);
+      outer_p<false>(p1, s0, vp);
+    }
+  } else {
+    const int mu = pass - 1;
+    int c[4];
+    site_coords(a.g, i, c);
+    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    cplx<float> u[3][3];
+    LinkIO<PL>::load(a.links, V, mu, i, u);
+    if (mu == 3 && c[3] == a.g.L[3] - 1 && a.g.bc < 0) {  // boundary sign folded into the link
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) u[x][y] = mk<float>(-u[x][y].re, -u[x][y].im);
+    }
+    for (int r = 0; r < a.nsrc; ++r) {
+      cplx<float> t[12], s0[12];
+      SpinP tp, w;
+      SpinorIO<PS>::load(a.s, V, r, nf, t);
+      pack_spin(tp, t);
+      matvec_p(w, u, tp);                  // U s(y+mu)
+      SpinorIO<PS>::load(a.s, V, r, i, s0);
+      outer_p<false>(p0, s0, w);
+      SpinorIO<PS>::load(a.v, V, r, i, t);
+      pack_spin(tp, t);
+      outer_p<true>(p1, w, tp);            // - conj(U s(y+mu)) v(y)
+      SpinorIO<PS>::load(a.v, V, r, nf, t);
+      pack_spin(tp, t);
+      matvec_p(w, u, tp);                  // U v(y+mu)
+      outer_p<false>(p1, s0, w);
+    }
+    scale = 0.25f;
+  }
+  cplx<float> m0[16], m1[16];
+  unpack_mat(m0, p0);
+  unpack_mat(m1, p1);
+  if (pass != 0) {  // D^0 = M - M^dag (before the g_a row factor)
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = p; q < 4; ++q) {
+        const cplx<float> x = m0[4 * p + q], y = m0[4 * q + p];
+        m0[4 * p + q] = mk<float>(x.re - y.re, x.im + y.im);
+        m0[4 * q + p] = mk<float>(y.re - x.re, y.im + x.im);
+      }
+  }
+  cplx<float>* out = a.F + (size_t)pass * NF * V + i;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float ga = (k < 8) ? scale : -scale;  // row a = k / 4: g5 = +1 for a < 2
+    out[(size_t)k * V] = ga * m0[k];
+    out[(size_t)(16 + k) * V] = ga * m1[k];
+  }
+}
+
 __device__ __forceinline__ void twiddle(cplx<float>& o, int m, int L) {
   float sn, cs;
   sincospif(2.0f * (float)m / (float)L, &sn, &cs);
@@ -740,7 +896,11 @@ int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsr
   const unsigned nblk = (unsigned)((g->geom.V + FLD_BS - 1) / FLD_BS);
   count_launches(1);
   if (ev_f) TSM_TRY(ev_f->begin(st));
-  contract_fields_kernel<R, PS, PL><<<nblk * 5, FLD_BS, 0, st>>>(a);
+  if constexpr (std::is_same<R, float>::value) {
+    contract_fields_pairs_kernel<PS, PL><<<nblk * 5, FLD_BS, 0, st>>>(a);
+  } else {
+    contract_fields_kernel<R, PS, PL><<<nblk * 5, FLD_BS, 0, st>>>(a);
+  }
   if (ev_f) TSM_TRY(ev_f->end(st));
   TSM_CUDA(cudaGetLastError());
   if (ev_xy) TSM_TRY(ev_xy->begin(st));

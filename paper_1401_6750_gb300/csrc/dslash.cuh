@@ -14,6 +14,10 @@
 // runs over (site tile, right-hand side) with the right-hand side fastest, so
 // the blocks of all right-hand sides of one site tile are scheduled back to
 // back and re-read that tile's links from L2 rather than from HBM.
+//
+// FP32 arithmetic (FP32, FP16 and BF16 fields) runs the colour products and
+// accumulations in packed pairs (two-wide FP32 FMA) with the two projected
+// spins side by side; FP64 and float-float sums use the scalar forms.
 #pragma once
 
 #include <type_traits>
@@ -25,14 +29,15 @@ namespace tsm {
 constexpr int DSLASH_BS = 128;
 
 // Resident blocks per SM the register allocation must allow (__launch_bounds__),
-// per field precision, as measured at 24^3 x 48: FP32 and 16-bit fields 6
-// (<= 80 registers), float-float 3 (<= 168); FP64 keeps the compiler's choice.
+// per field precision, as measured at 24^3 x 48: FP32 and 16-bit fields 7
+// (<= 72 registers; 6 was 2.5% slower on the whole TSM step, 8 spills),
+// float-float 3 (<= 168); FP64 keeps the compiler's choice.
 // TSM_DSLASH_MINB32 / _MINB16 / _MINBDS override them (variant builds).
 #ifndef TSM_DSLASH_MINB32
-#define TSM_DSLASH_MINB32 6
+#define TSM_DSLASH_MINB32 7
 #endif
 #ifndef TSM_DSLASH_MINB16
-#define TSM_DSLASH_MINB16 6
+#define TSM_DSLASH_MINB16 7
 #endif
 #ifndef TSM_DSLASH_MINBDS
 #define TSM_DSLASH_MINBDS 3
@@ -412,17 +417,160 @@ __device__ __forceinline__ void stencil_rolled(cplx<R> (&acc)[NR][12], const Dsl
   }
 }
 
+// One hop in packed-pair arithmetic (Blackwell's two-wide FP32 FMA,
+// __ffma2_rn): the two projected spins travel together as pairs
+// hr[b] = (h0[b].re, h1[b].re), hi[b] = (h0[b].im, h1[b].im), so that one
+// two-wide FMA serves both spins.  Results come back per spin pair:
+// up[0..2] = (spin 0, spin 1) real parts, up[3..5] imaginary parts, and lo[]
+// likewise for spins (2, 3), except that for MU = x, y (whose lower spins
+// take the other upper spin) lo holds (spin 3, spin 2).
+__device__ __forceinline__ float2 bcast2(float v) { return make_float2(v, v); }
+
+template <int MU, int S, bool DAG, bool FIRST>
+__device__ __forceinline__ void hop_pairs(float2 (&up)[6], float2 (&lo)[6], const cplx<float> (&h0)[3],
+                                          const cplx<float> (&h1)[3], const cplx<float> (&u)[3][3], float sgn) {
+  float2 hr[3], hi[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    hr[b] = make_float2(h0[b].re, h1[b].re);
+    hi[b] = make_float2(h0[b].im, h1[b].im);
+  }
+  float2 wr[3], wi[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      // W = U (or U^dag): w = W h;  W_ab = (ur, ui)
+      const float ur = DAG ? u[b][a].re : u[a][b].re;
+      const float ui = DAG ? -u[b][a].im : u[a][b].im;
+      if (b == 0) {
+        wr[a] = __fmul2_rn(bcast2(ur), hr[0]);
+        wi[a] = __fmul2_rn(bcast2(ur), hi[0]);
+      } else {
+        wr[a] = __ffma2_rn(bcast2(ur), hr[b], wr[a]);
+        wi[a] = __ffma2_rn(bcast2(ur), hi[b], wi[a]);
+      }
+      wr[a] = __ffma2_rn(bcast2(-ui), hi[b], wr[a]);
+      wi[a] = __ffma2_rn(bcast2(ui), hr[b], wi[a]);
+    }
+  }
+  // upper spins: + sgn w;  lower spins per projector (see hop_accumulate)
+  const float s = (float)S * sgn;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (FIRST) {
+      up[a] = __fmul2_rn(bcast2(sgn), wr[a]);
+      up[3 + a] = __fmul2_rn(bcast2(sgn), wi[a]);
+    } else {
+      up[a] = __ffma2_rn(bcast2(sgn), wr[a], up[a]);
+      up[3 + a] = __ffma2_rn(bcast2(sgn), wi[a], up[3 + a]);
+    }
+    float2 cr, ci, vr, vi;  // lo += cr * vr (real pair), ci * vi (imaginary pair)
+    if (MU == 0) {          // (s3, s2) += S i (w0, w1)
+      cr = bcast2(-s); vr = wi[a];
+      ci = bcast2(s);  vi = wr[a];
+    } else if (MU == 1) {   // (s3, s2) += S (-w0, w1)
+      cr = make_float2(-s, s); vr = wr[a];
+      ci = make_float2(-s, s); vi = wi[a];
+    } else if (MU == 2) {   // (s2, s3) += S i (w0, -w1)
+      cr = make_float2(-s, s); vr = wi[a];
+      ci = make_float2(s, -s); vi = wr[a];
+    } else {                // (s2, s3) += S sgn (w0, w1)
+      cr = bcast2(s); vr = wr[a];
+      ci = bcast2(s); vi = wi[a];
+    }
+    if (FIRST) {
+      lo[a] = __fmul2_rn(cr, vr);
+      lo[3 + a] = __fmul2_rn(ci, vi);
+    } else {
+      lo[a] = __ffma2_rn(cr, vr, lo[a]);
+      lo[3 + a] = __ffma2_rn(ci, vi, lo[3 + a]);
+    }
+  }
+}
+
+// Both hops of direction MU for NR right-hand sides in packed pairs (each
+// link loaded and rebuilt once); FIRST initialises the accumulators.
+template <int MU, int SF, int PIN, int PL, int NR, bool EO, bool FIRST>
+__device__ __forceinline__ void pairs_dir(float2 (&up)[NR][6], float2 (&lo)[NR][6], const DslashArgs& a, int r0,
+                                          const bool (&act)[NR], int i, const int c[4]) {
+  const size_t V = (size_t)a.g.V;
+  const size_t FS = EO ? V / 2 : V;
+  const int stride = dir_stride(a.g, MU);
+  cplx<float> u[3][3], h0[3], h1[3];
+  {
+    const int n = fwd_site(a.g, i, c, MU, stride);
+    LinkIO<PL>::load(a.links, V, MU, i, u);
+    const float sgn = (MU == 3 && c[3] == a.g.L[3] - 1) ? (float)a.g.bc : 1.0f;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) {  // inactive slots are never read; FIRST still defines them
+        if (FIRST) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) up[j][k] = lo[j][k] = make_float2(0.0f, 0.0f);
+        }
+        continue;
+      }
+      ProjLoad<MU, SF, PIN, float>::run(h0, h1, a.in, FS, r0 + j, EO ? (n >> 1) : n);
+      hop_pairs<MU, SF, false, FIRST>(up[j], lo[j], h0, h1, u, sgn);
+    }
+  }
+  {
+    const int n = bwd_site(a.g, i, c, MU, stride);
+    LinkIO<PL>::load(a.links, V, MU, n, u);
+    const float sgn = (MU == 3 && c[3] == 0) ? (float)a.g.bc : 1.0f;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      if (!act[j]) continue;
+      ProjLoad<MU, -SF, PIN, float>::run(h0, h1, a.in, FS, r0 + j, EO ? (n >> 1) : n);
+      hop_pairs<MU, -SF, true, false>(up[j], lo[j], h0, h1, u, sgn);
+    }
+  }
+}
+
+// All eight hops of one site in packed pairs, for NR right-hand sides; out
+// receives the hop sum in component order.  Directions x and y leave the
+// lower spins in (3, 2) order; one swap before z restores (2, 3).
+template <int SF, int PIN, int PL, int NR, bool EO>
+__device__ __forceinline__ void stencil_pairs(cplx<float> (&out)[NR][12], const DslashArgs& a, int r0,
+                                              const bool (&act)[NR], int i, const int c[4]) {
+  float2 up[NR][6], lo[NR][6];
+  pairs_dir<0, SF, PIN, PL, NR, EO, true>(up, lo, a, r0, act, i, c);
+  pairs_dir<1, SF, PIN, PL, NR, EO, false>(up, lo, a, r0, act, i, c);
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) lo[j][k] = make_float2(lo[j][k].y, lo[j][k].x);
+  pairs_dir<2, SF, PIN, PL, NR, EO, false>(up, lo, a, r0, act, i, c);
+  pairs_dir<3, SF, PIN, PL, NR, EO, false>(up, lo, a, r0, act, i, c);
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      out[j][col] = mk<float>(up[j][col].x, up[j][3 + col].x);
+      out[j][3 + col] = mk<float>(up[j][col].y, up[j][3 + col].y);
+      out[j][6 + col] = mk<float>(lo[j][col].x, lo[j][3 + col].x);
+      out[j][9 + col] = mk<float>(lo[j][col].y, lo[j][3 + col].y);
+    }
+}
+
 // Full operator at site i for NR right-hand sides: out = in + i tw g5 in - kappa * hop.
-template <int SF, typename R, int PIN, int PL, int NR>
+template <int SF, typename R, int PIN, int PL, int NR, bool P2 = std::is_same<R, float>::value>
 __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0, const bool (&act)[NR],
                                            int i) {
   int c[4];
   site_coords(a.g, i, c);
+  if constexpr (P2 && std::is_same<R, float>::value) {
+    stencil_pairs<SF, PIN, PL, NR, false>(out, a, r0, act, i, c);
+  } else {
 #pragma unroll
-  for (int j = 0; j < NR; ++j)
+    for (int j = 0; j < NR; ++j)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[j][k] = mk<R>(0, 0);
-  if constexpr (std::is_same<R, dsf>::value) {
+      for (int k = 0; k < 12; ++k) out[j][k] = mk<R>(0, 0);
+  }
+  if constexpr (P2 && std::is_same<R, float>::value) {
+    // done above
+  } else if constexpr (std::is_same<R, dsf>::value) {
     stencil_rolled<SF, R, PIN, PL, NR, false>(out, a, r0, act, i, c);
   } else {
     stencil_dir<0, SF, R, PIN, PL, NR>(out, a, r0, act, i, c);
@@ -503,7 +651,7 @@ __device__ __forceinline__ void reduce_and_finalize(const Epi& epi, const RedSlo
 // One block of work: bid = site_block * ngroups + group, group = NR
 // consecutive right-hand sides.  Shared by the single-instance kernel below
 // and the multi-instance kernels of the batched solver.
-template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+template <typename R, int SF, int PIN, int PL, int NR, class Epi, bool P2 = std::is_same<R, float>::value>
 __device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi, int bid) {
   __shared__ double sh[32];
   const int ngrp = (a.nrhs + NR - 1) / NR;
@@ -524,7 +672,7 @@ __device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi
   for (int j = 0; j < NR; ++j) red[j] = (R)0;
   if (i < a.g.V) {
     cplx<R> out[NR][12];
-    apply_site<SF, R, PIN, PL, NR>(out, a, r0, act, i);
+    apply_site<SF, R, PIN, PL, NR, P2>(out, a, r0, act, i);
 #pragma unroll
     for (int j = 0; j < NR; ++j)
       if (act[j]) red[j] = epi.site(r0 + j, i, out[j]);
@@ -536,9 +684,9 @@ __device__ __forceinline__ void dslash_block(const DslashArgs& a, const Epi& epi
   }
 }
 
-template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+template <typename R, int SF, int PIN, int PL, int NR, class Epi, bool P2 = std::is_same<R, float>::value>
 __global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_kernel(DslashArgs a, Epi epi) {
-  dslash_block<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
+  dslash_block<R, SF, PIN, PL, NR, Epi, P2>(a, epi, blockIdx.x);
 }
 
 // ---------------------------------------------------------------- even-odd operator
@@ -552,16 +700,22 @@ __device__ __forceinline__ int eo_site(const Geom& g, int j, int p, int c[4]) {
   return i0 + b;
 }
 
-template <int SF, typename R, int PIN, int PL, int NR>
+template <int SF, typename R, int PIN, int PL, int NR, bool P2 = std::is_same<R, float>::value>
 __device__ __forceinline__ void apply_site_eo(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0,
                                               const bool (&act)[NR], int j) {
   int c[4];
   const int i = eo_site(a.g, j, a.parity, c);
+  if constexpr (P2 && std::is_same<R, float>::value) {
+    stencil_pairs<SF, PIN, PL, NR, true>(out, a, r0, act, i, c);
+  } else {
 #pragma unroll
-  for (int q = 0; q < NR; ++q)
+    for (int q = 0; q < NR; ++q)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[q][k] = mk<R>(0, 0);
-  if constexpr (std::is_same<R, dsf>::value) {
+      for (int k = 0; k < 12; ++k) out[q][k] = mk<R>(0, 0);
+  }
+  if constexpr (P2 && std::is_same<R, float>::value) {
+    // done above
+  } else if constexpr (std::is_same<R, dsf>::value) {
     stencil_rolled<SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
   } else {
     stencil_dir<0, SF, R, PIN, PL, NR, true>(out, a, r0, act, i, c);
@@ -591,7 +745,7 @@ __device__ __forceinline__ void apply_site_eo(cplx<R> (&out)[NR][12], const Dsla
   }
 }
 
-template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+template <typename R, int SF, int PIN, int PL, int NR, class Epi, bool P2 = std::is_same<R, float>::value>
 __device__ __forceinline__ void dslash_block_eo(const DslashArgs& a, const Epi& epi, int bid) {
   __shared__ double sh[32];
   const int ngrp = (a.nrhs + NR - 1) / NR;
@@ -612,7 +766,7 @@ __device__ __forceinline__ void dslash_block_eo(const DslashArgs& a, const Epi& 
   for (int q = 0; q < NR; ++q) red[q] = (R)0;
   if (j < a.g.V / 2) {
     cplx<R> out[NR][12];
-    apply_site_eo<SF, R, PIN, PL, NR>(out, a, r0, act, j);
+    apply_site_eo<SF, R, PIN, PL, NR, P2>(out, a, r0, act, j);
 #pragma unroll
     for (int q = 0; q < NR; ++q)
       if (act[q]) red[q] = epi.site(r0 + q, j, out[q]);
@@ -624,9 +778,9 @@ __device__ __forceinline__ void dslash_block_eo(const DslashArgs& a, const Epi& 
   }
 }
 
-template <typename R, int SF, int PIN, int PL, int NR, class Epi>
+template <typename R, int SF, int PIN, int PL, int NR, class Epi, bool P2 = std::is_same<R, float>::value>
 __global__ void __launch_bounds__(DSLASH_BS, MinBlocks<PIN>::value) dslash_eo_kernel(DslashArgs a, Epi epi) {
-  dslash_block_eo<R, SF, PIN, PL, NR, Epi>(a, epi, blockIdx.x);
+  dslash_block_eo<R, SF, PIN, PL, NR, Epi, P2>(a, epi, blockIdx.x);
 }
 
 // a.nblk must be ceil(V/2 / DSLASH_BS); nr right-hand sides per thread (1, 2
