@@ -288,6 +288,46 @@ def probe(args):
     ctx.close()
 
 
+def lp_variants(g, abi, torch, w, flag, hp_solver, moms, n_lp, n_hp, steps=2):
+    """The same TSM step (n_lp bulk + n_hp correction sources) with the bulk
+    LP solves at 12 right-hand sides per launch (FP16) and at 32 with BF16
+    storage: the other two launch shapes of the 24^3x48 batched workload.
+    One warm-up step, then `steps` steps timed with CUDA events."""
+    import ctypes
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    n_out = 160 * moms.shape[0] * w["dims"][3] * 2
+    out = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    res = []
+    for nrhs, lp_name in ((12, "f16"), (32, "bf16")):
+        lp = (abi.TSM_SOLVER_LP_F16 if lp_name == "f16" else abi.TSM_SOLVER_LP_BF16) | flag
+
+        def step(k):
+            p = abi.tsm_params(w["kappa"], w["mu"], n_lp, n_hp, w["rho_lp"], w["rho_hp"], lp, hp_solver,
+                               77003 + 7919 * k, 20000, nrhs, moms.shape[0],
+                               moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+            st = abi.tsm_stats()
+            abi.check(abi.lib().tsm_solve_tsm_dev(g.handle, ctypes.byref(p), ctypes.c_void_p(out.data_ptr()), None,
+                                                  ctypes.byref(st), sp), "tsm_solve_tsm_dev")
+            return st
+        step(0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = []
+        for k in range(steps):
+            st = step(1 + k)
+            its.append(st.lp_iterations_total / (n_lp + n_hp))
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        res.append({"nrhs_per_launch": nrhs, "lp_storage": lp_name, "sources_per_step": n_lp + n_hp,
+                    "sources_per_s": (n_lp + n_hp) * steps / t, "ms_per_step": t / steps * 1e3,
+                    "lp_iterations_mean": round(sum(its) / len(its), 1)})
+    return res
+
+
 def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs=32):
     """TSM against the plain high-precision path at equal final loop accuracy.
 
@@ -612,6 +652,10 @@ def main():
     if rank == 0 and not args.no_equal_accuracy:
         eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver)
 
+    variants = None
+    if rank == 0 and not args.no_tdil:
+        variants = lp_variants(g, abi, torch, w, flag, hp_solver, moms, args.nrhs, args.n_hp)
+
     tdil = None
     hpe_var = None
     binstore = None
@@ -647,6 +691,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
             "equal_accuracy": eq,
+            "launch_shapes": variants,
             "time_dilution": tdil,
             "hpe": hpe_var,
             "binary_storage": binstore,
