@@ -137,7 +137,17 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
     // has its own workspaces (slot 1) and solution buffer; the host waits of
     // the solvers' convergence checks happen in each thread independently.
     if (!g->aux_stream) {
-      TSM_CUDA(cudaStreamCreateWithFlags(&g->aux_stream, cudaStreamNonBlocking));
+      // The correction chain (many small latency-bound launches) gets the
+      // highest stream priority, so that its blocks are scheduled beside the
+      // bulk's arithmetic-bound blocks as soon as slots free up.
+      // TSM_AUX_PRIORITY=0 creates it at the default priority (measurements).
+      static const bool prio = [] {
+        const char* e = getenv("TSM_AUX_PRIORITY");
+        return !(e && atoi(e) == 0);
+      }();
+      int least = 0, greatest = 0;
+      TSM_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      TSM_CUDA(cudaStreamCreateWithPriority(&g->aux_stream, cudaStreamNonBlocking, prio ? greatest : least));
       TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[0], cudaEventDisableTiming));
       TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[1], cudaEventDisableTiming));
     }
