@@ -341,7 +341,13 @@ typedef struct {
  * sums of single sources.  loops_host: [160][n_mom][T][2] doubles.
  * parts_host (optional): the three source-summed accumulators
  * [3][160][n_mom][T][2] in the order bulk-LP, corr-HP, corr-LP.  Synchronises
- * `stream`. */
+ * `stream`.
+ * Concurrency: when n_hp > 0 the correction sources' HP and LP solves run from
+ * a library worker thread on a second stream that the gauge handle owns,
+ * created at the device's highest stream priority, beside the bulk solves on
+ * `stream`; the call returns after both, with `stream` ordered after the
+ * second stream's work.  TSM_STREAMS=1 in the environment runs everything on
+ * `stream` from the calling thread. */
 int tsm_solve_tsm(tsm_gauge* g, const tsm_params* p, double* loops_host,
                   double* parts_host, tsm_stats* stats, void* stream);
 
