@@ -23,6 +23,7 @@
 #include "dslash.cuh"
 #include "internal.h"
 #include "solver_kernels.cuh"
+#include "tc_hop.cuh"
 
 namespace tsm {
 
@@ -217,16 +218,16 @@ struct SolverEO {
     const size_t Vh = (size_t)g->geom.V / 2;
     EpiStore<Rs, T::PS> es{w.tes.p, Vh, 0, RedSlots{nullptr, nullptr}};
     // q = Mhat p
-    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
+    launch_dslash_eo_tc<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
     {
       EpiMp<Rs, T::PS> e{w.q.p, Vh, w.st.as<RhsState>(), slots(w)};
-      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
+      launch_dslash_eo_tc<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
     }
     // Ap = Mhat^dag q; r -= alpha Ap; x += alpha p
-    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
+    launch_dslash_eo_tc<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, Vh, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo_tc<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
     }
     dim3 eg(((int)Vh + EW_BS - 1) / EW_BS, nrhs);
     k_pupdate<T::PA, T::PS><<<eg, EW_BS, 0, s>>>(w.r.p, w.p.p, w.st.as<RhsState>(), 0, (int)Vh);
@@ -246,21 +247,21 @@ struct SolverEO {
     EpiStore<Rs, T::PS> es{w.tes.p, Vh, 0, RedSlots{nullptr, nullptr}};
     EventPair ev[5];
     TSM_TRY(ev[0].begin(s));
-    launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
+    launch_dslash_eo_tc<Rs, -1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.p.p, kappa, mup, nrhs), es, s);
     TSM_TRY(ev[0].end(s));
     TSM_TRY(ev[1].begin(s));
     {
       EpiMp<Rs, T::PS> e{w.q.p, Vh, w.st.as<RhsState>(), slots(w)};
-      launch_dslash_eo<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
+      launch_dslash_eo_tc<Rs, -1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.p.p, kappa, mup, nrhs), e, s);
     }
     TSM_TRY(ev[1].end(s));
     TSM_TRY(ev[2].begin(s));
-    launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
+    launch_dslash_eo_tc<Rs, +1, T::PS, T::PLs>(w.nr_s, step_a(g, T::PLs, w.q.p, kappa, -mup, nrhs), es, s);
     TSM_TRY(ev[2].end(s));
     TSM_TRY(ev[3].begin(s));
     {
       EpiCG<Rs, T::PA, T::PS> e{w.r.p, w.x.p, w.p.p, Vh, w.st.as<RhsState>(), slots(w), prm};
-      launch_dslash_eo<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
+      launch_dslash_eo_tc<Rs, +1, T::PS, T::PLs>(w.nr_s, step_b(g, T::PLs, w.tes.p, w.q.p, kappa, -mup, nrhs), e, s);
     }
     TSM_TRY(ev[3].end(s));
     TSM_TRY(ev[4].begin(s));
@@ -494,9 +495,9 @@ void mhat_launch(const tsm_gauge* g, double kappa, double tau, const void* in_o,
   const double d = 1.0 + tau * tau;
   EpiStore<R, P> et{t_e, Vh, 0, RedSlots{nullptr, nullptr}};
   EpiStore<R, P> eo{out_o, Vh, 0, RedSlots{nullptr, nullptr}};
-  launch_dslash_eo<R, SF, P, P>(1, eo_args(g, P, in_o, nullptr, 0, kappa, 0.0, 0.0, -kappa / d, kappa * tau / d, nrhs),
+  launch_dslash_eo_tc<R, SF, P, P>(1, eo_args(g, P, in_o, nullptr, 0, kappa, 0.0, 0.0, -kappa / d, kappa * tau / d, nrhs),
                                 et, s);
-  launch_dslash_eo<R, SF, P, P>(1, eo_args(g, P, t_e, in_o, 1, kappa, 1.0, tau, kappa, 0.0, nrhs), eo, s);
+  launch_dslash_eo_tc<R, SF, P, P>(1, eo_args(g, P, t_e, in_o, 1, kappa, 1.0, tau, kappa, 0.0, nrhs), eo, s);
 }
 
 template <typename R, int P>
