@@ -70,28 +70,50 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
+        self.lines = []  # (perf_counter time, line)
+        self.reader = None
 
     def start(self):
+        """Start sampling every 50 ms and wait (at most 3 s) for the first
+        sample, so that the timed region is covered from its start."""
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return
 
-    def stop(self):
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.perf_counter(), line))
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        t_end = time.perf_counter() + 3.0
+        while not self.lines and time.perf_counter() < t_end:
+            time.sleep(0.01)
+
+    def stop(self, t0=None, t1=None):
+        """Samples taken between perf_counter times t0 and t1 (all samples if
+        none fall inside)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
+            self.proc.wait()
+        if self.reader is not None:
+            self.reader.join(timeout=5)
+        lines = [ln for t, ln in self.lines if t0 is None or (t0 <= t <= t1)]
+        if not lines:
+            lines = [ln for _, ln in self.lines]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -592,13 +614,15 @@ def main():
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.perf_counter()
     e0.record(stream)
     for k in range(args.steps):
         step_dev(args.warmup + k)
     e1.record(stream)
     e1.synchronize()
+    t_wall1 = time.perf_counter()
     elapsed = e0.elapsed_time(e1) * 1e-3
-    clk = clocks.stop()
+    clk = clocks.stop(t_wall0, t_wall1)
     launches = lib.tsm_kernel_launches() - launches0
     barrier()
     elapsed = max_over_ranks(elapsed)

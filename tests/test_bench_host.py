@@ -1,0 +1,73 @@
+"""Host logic of bench.py that needs no GPU: the clock sampler.
+
+A stand-in `nvidia-smi` on PATH prints the queried fields every 50 ms (first
+clocks at 2070 MHz with no throttle reason, then 1500 MHz with sw_power_cap
+active); the sampler must keep only the samples taken inside the window it is
+given, take their median SM clock and report the active reasons.
+"""
+import os
+import stat
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FAKE = """#!/bin/sh
+n=0
+while true; do
+  if [ $n -lt 10 ]; then
+    echo "2070, 2070, 900.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active"
+  else
+    echo "1500, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active"
+  fi
+  n=$((n + 1))
+  sleep 0.05
+done
+"""
+
+
+def _with_fake(tmp_path, monkeypatch):
+    exe = tmp_path / "nvidia-smi"
+    exe.write_text(FAKE)
+    exe.chmod(exe.stat().st_mode | stat.S_IEXEC)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ.get("PATH", ""))
+
+
+def test_sampler_keeps_window_and_reports_reasons(tmp_path, monkeypatch):
+    _with_fake(tmp_path, monkeypatch)
+    import bench
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.lines, "sampler returned before its first sample"
+    t0 = time.perf_counter()
+    time.sleep(0.2)             # samples of the first phase (2070 MHz, 0.5 s long)
+    t1 = time.perf_counter()
+    time.sleep(0.6)             # later samples (1500 MHz, power cap) fall outside [t0, t1]
+    early = c.stop(t0, t1)
+    assert early["sm_mhz"] == 2070.0 and early["reasons"] == [], early
+    assert early["samples"] >= 1
+
+
+def test_sampler_sees_power_cap(tmp_path, monkeypatch):
+    _with_fake(tmp_path, monkeypatch)
+    import bench
+    c = bench.ClockSampler(0)
+    c.start()
+    time.sleep(0.8)
+    t0 = time.perf_counter()
+    time.sleep(0.3)
+    t1 = time.perf_counter()
+    late = c.stop(t0, t1)
+    assert late["sm_mhz"] == 1500.0, late
+    assert late["sm_max_mhz"] == 2070.0
+    assert late["reasons"] == ["sw_power_cap"]
+
+
+def test_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    monkeypatch.setenv("PATH", str(tmp_path))
+    import bench
+    c = bench.ClockSampler(0)
+    c.start()
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
