@@ -88,3 +88,25 @@ def test_empty_batches(ctx):
     torch.cuda.synchronize()
     assert torch.all(sentinel == 3.0)
     g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(abi.TSM_F64, 1e-11), (abi.TSM_F32, 1e-6)])
+def test_largest_momentum_radius(ctx, prec, tol):
+    """Momentum components up to the accepted maximum |n| = 8 (the x/y
+    transform then keeps 17 x 17 partial sums per field), larger than the
+    extents (the phases alias), against the oracle's direct Fourier sums;
+    |n| = 9 is refused."""
+    dims, kappa, mu = (6, 4, 8, 4), 0.125, 0.01
+    g, links = gauge(ctx, dims, 0.3, 9, -1)
+    u = lattice.effective_links(links, -1)
+    s = round_to(synth.gaussian_spinor(dims, 63, nrhs=2), prec)
+    moms = [(8, 0, 0), (-8, 3, 0), (0, 8, -8), (5, -7, 2), (0, 0, 0)]
+    nat = g.pack(to_device(s), prec)
+    out = api.loops_complex(g.contract(kappa, mu, prec, nat, 2, moms))
+    want = sum(contract.project(contract.loop_densities(u, s[r], kappa, mu), dims, moms) for r in range(2))
+    for ins in range(160):
+        err = np.linalg.norm(out[ins] - want[ins]) / np.linalg.norm(want[ins])
+        assert err < tol, (ins, err)
+    with pytest.raises(abi.TsmError):
+        g.contract(kappa, mu, prec, nat, 2, [(9, 0, 0)])
+    g.close()
