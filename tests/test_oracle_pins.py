@@ -243,10 +243,13 @@ def test_dense_traces_free_field_closed_form(dims, t_bc):
     assert np.sum(np.abs(cf) > 1e-3 * scale) == 3 + sum(L > 2 for L in dims[:3])
 
 
-def test_one_end_identity_unit_sources():
-    """Summed over all 12V unit-vector sources the estimators are exact."""
+@pytest.mark.parametrize("mu", [0.05, 0.0])
+def test_one_end_identity_unit_sources(mu):
+    """Summed over all 12V unit-vector sources the estimators are exact.  At
+    mu = 0 (G_u = G_d = A^-1) the tau_3 estimator vanishes identically and
+    the other gives 2 Tr[X A^-1] (g5-hermiticity of A)."""
     dims = RNG_DIMS
-    kappa, mu = 0.12, 0.05
+    kappa = 0.12
     u = lattice.effective_links(synth.gauge_links(dims, 0.5, 21), -1)
     g_u, _ = dense.propagators(u, dims, kappa, mu)
     n = g_u.shape[0]
