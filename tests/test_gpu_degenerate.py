@@ -110,3 +110,22 @@ def test_largest_momentum_radius(ctx, prec, tol):
     with pytest.raises(abi.TsmError):
         g.contract(kappa, mu, prec, nat, 2, [(9, 0, 0)])
     g.close()
+
+
+@pytest.mark.parametrize("solver_kind,eo,bad", [(abi.TSM_SOLVER_F64, 0, np.nan),
+                                                (abi.TSM_SOLVER_LP_F16, abi.TSM_SOLVER_EO, np.inf),
+                                                (abi.TSM_SOLVER_F32_RELIABLE, abi.TSM_SOLVER_EO, np.nan)])
+def test_nonfinite_right_hand_side_reported(ctx, solver_kind, eo, bad):
+    """A NaN or Inf in a caller's right-hand side ends that right-hand side's
+    CG as a breakdown (its |b|^2 is not finite) and the call returns
+    TSM_ERR_NONFINITE, without hanging."""
+    dims, kappa, mu = (4, 4, 4, 4), 0.125, 0.01
+    g, _ = gauge(ctx, dims, 0.3, 10, -1)
+    prec = api.solution_prec(solver_kind)
+    b = synth.gaussian_spinor(dims, 64, nrhs=2)
+    b[1].flat[17] = bad
+    nb = g.pack(to_device(b), prec)
+    with pytest.raises(abi.TsmError) as e:
+        g.invert(abi.TSM_OP_M, kappa, mu, solver_kind | eo, 1e-2, nb, 2)
+    assert e.value.code == abi.TSM_ERR_NONFINITE
+    g.close()
