@@ -49,25 +49,33 @@ def bilinear(a, g, b):
     return np.einsum("...sc,sr,...rc->...", np.conj(a), g, b)
 
 
-def loop_densities_pair(u, a, b, kappa, mu, prefactor_derivative=False):
+def loop_densities_pair(u, a, b, kappa, mu, prefactor_derivative=False, only=None, chi1=None):
     """The sesquilinear form behind the loop densities: phi = g5 a on the left,
     chi_0 = b and chi_1 = g5 A b on the right, so loop_densities(s) is the
     pair (s, s).  With prefactor_derivative the flavour prefactors are
-    replaced by their mu-derivatives (-2 i mu' -> -4 i kappa, 2 -> 0)."""
+    replaced by their mu-derivatives (-2 i mu' -> -4 i kappa, 2 -> 0).
+    ``only`` (a collection of insertion indices) skips every other insertion,
+    leaving it zero: the same formulas, evaluated for a subset (large
+    lattices).  ``chi1``, if given, is g5 A b computed beforehand (the same
+    field, so that several subsets of one source share it)."""
     mu_p = 2.0 * kappa * mu
+    want = (lambda i: True) if only is None else (lambda i: i in only)
     phi = dirac.gamma5(a)
-    v = dirac.gamma5(dirac.apply_A(u, b, kappa))
+    v = dirac.gamma5(dirac.apply_A(u, b, kappa)) if chi1 is None else chi1
     prefs = (-4j * kappa, 0.0) if prefactor_derivative else (-2j * mu_p, 2.0)
     out = np.zeros((N_INSERTIONS,) + a.shape[:-2], dtype=np.complex128)
     for flavour, (chi, pref) in enumerate(((b, prefs[0]), (v, prefs[1]))):
         if pref == 0.0:
             continue
         for g in range(16):
-            out[insertion_index(flavour, False, 0, g)] = pref * bilinear(phi, INSERTIONS[g], chi)
+            if want(insertion_index(flavour, False, 0, g)):
+                out[insertion_index(flavour, False, 0, g)] = pref * bilinear(phi, INSERTIONS[g], chi)
         for m in range(4):
             um = u[..., m, :, :]
             ub = lattice.bwd(um, m)
             for g in range(16):
+                if not want(insertion_index(flavour, True, m, g)):
+                    continue
                 gm = INSERTIONS[g]
                 t1 = bilinear(phi, gm, dirac.colour_mul(um, lattice.fwd(chi, m)))
                 t2 = bilinear(lattice.fwd(phi, m), gm, dirac.colour_mul_dag(um, chi))
@@ -77,13 +85,14 @@ def loop_densities_pair(u, a, b, kappa, mu, prefactor_derivative=False):
     return out
 
 
-def loop_densities(u, s, kappa, mu):
+def loop_densities(u, s, kappa, mu, only=None):
     """Per-site densities of all 160 insertions for one solved source s.
 
     ``u`` are effective links; ``s`` may carry leading batch axes (several
-    sources).  Returns complex128 (160, ..., t, z, y, x).
+    sources).  Returns complex128 (160, ..., t, z, y, x); with ``only``, the
+    insertions not listed are left zero.
     """
-    return loop_densities_pair(u, s, s, kappa, mu)
+    return loop_densities_pair(u, s, s, kappa, mu, only=only)
 
 
 def phases(dims, moms):

@@ -343,3 +343,29 @@ def test_tsm_unbiased_against_exact():
             d = est[ins, 0, t] - exact[ins, 0, t]
             assert abs(d.real) <= 4 * sig[ins, 0, t].real + 1e-12
             assert abs(d.imag) <= 4 * sig[ins, 0, t].imag + 1e-12
+
+
+def test_density_subset_equals_full():
+    """loop_densities(only=...) evaluates the same formulas for the listed
+    insertions and leaves the rest zero."""
+    dims = (2, 2, 2, 4)
+    u = lattice.effective_links(synth.gauge_links(dims, 0.4, 61), -1)
+    s = synth.gaussian_spinor(dims, 62)
+    full = contract.loop_densities(u, s, 0.12, 0.05)
+    sel = {0, 15, 17, 95, 152}
+    part = contract.loop_densities(u, s, 0.12, 0.05, only=sel)
+    for i in range(contract.N_INSERTIONS):
+        if i in sel:
+            assert np.array_equal(part[i], full[i])
+        else:
+            assert not np.any(part[i])
+
+
+def test_density_given_chi1_equals_full():
+    """Passing g5 A s beforehand changes nothing."""
+    dims = (2, 2, 2, 4)
+    u = lattice.effective_links(synth.gauge_links(dims, 0.4, 63), -1)
+    s = synth.gaussian_spinor(dims, 64)
+    v = dirac.gamma5(dirac.apply_A(u, s, 0.12))
+    full = contract.loop_densities(u, s, 0.12, 0.05)
+    assert np.array_equal(contract.loop_densities_pair(u, s, s, 0.12, 0.05, chi1=v), full)
