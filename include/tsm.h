@@ -36,8 +36,19 @@
  * Ownership: the library owns contexts, gauge handles and its workspaces.
  *   Caller pointers are only used during the call (and the work it enqueues
  *   on the caller's stream); nothing is freed or retained.
- * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *   stream).  Calls that return host data synchronise that stream.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the context's
+ *   own blocking stream, ordered with the legacy default stream).  Calls that
+ *   return host data synchronise that stream.
+ * Threads: calls on one handle may come from several host threads and
+ *   streams.  The library's per-handle workspaces and scratch are guarded on
+ *   the host, and each one's use on the GPU is ordered across streams by an
+ *   event (a stream that takes it over waits for the previous user's last
+ *   launch).  Apart from tsm_create_gauge and tsm_destroy_gauge, which
+ *   synchronise the device, the library enqueues nothing on the legacy
+ *   default stream, so its calls do not invalidate a graph capture on another
+ *   thread's blocking stream.  Inside a capture the cross-stream event waits
+ *   are left out: captured calls on one handle must be ordered by the
+ *   caller.
  * Errors: every int-returning call returns TSM_OK (0) or a TSM_ERR_* code;
  *   tsm_last_error() gives a message for the calling thread.  No exception
  *   crosses the ABI.  A call that fails with TSM_ERR_INVALID_ARG has not
@@ -84,7 +95,7 @@ enum tsm_solver {
   TSM_SOLVER_F64 = 0,          /* FP64 links and vectors throughout             */
   TSM_SOLVER_F32_RELIABLE = 1, /* FP32 CG; true residual and solution sum in     *
                                 * float-float (about 44 significant bits), for  *
-                                * rho down to about 1e-10 (HP); tighter: F64    */
+                                * rho down to about 1e-9 (HP); tighter: F64     */
   TSM_SOLVER_LP_F16 = 2,       /* FP16 links/p/Ap, FP32 x and r (LP)            */
   TSM_SOLVER_LP_BF16 = 3,      /* BF16 links/p/Ap, FP32 x and r (LP)            */
   /* Flag OR-ed into any of the above: solve the even-odd (Schur complement)
@@ -179,10 +190,13 @@ int tsm_make_diluted_sources(tsm_gauge* g, uint64_t noise_seed,
 
 /* Solve M s_r = eta_r (Eq. 1) for the Z4 sources r = first_src ..
  * first_src + nsrc - 1 by CG on M^dag M with x0 = 0, stopping when the
- * iterated residual of the normal equations drops below rho and the true
- * residual (recomputed with the precise operator: FP64 for F64,
- * float-float for F32_RELIABLE, FP32 for the LP solvers) confirms it; otherwise the
- * iteration restarts from the true residual, up to max_iter in total.
+ * iterated residual of the normal equations drops below rho (1 - c) and the
+ * true residual (recomputed with the precise operator: FP64 for F64,
+ * float-float for F32_RELIABLE, FP32 for the LP solvers) confirms it;
+ * otherwise the iteration restarts from the true residual, up to max_iter in
+ * total.  c is a margin for the precise operator's own rounding (1e-6 FP64,
+ * 1e-2 float-float, 1e-3 FP32), so that the true residual of each returned
+ * solution, recomputed exactly, is at most rho.
  * Solutions are written in native layout: F64 for TSM_SOLVER_F64 and
  * TSM_SOLVER_F32_RELIABLE (its float-float accumulated solution), F32 for the LP
  * solvers.  stats_host (optional) receives nsrc records.  Returns
@@ -306,7 +320,8 @@ int tsm_contract_hpe(tsm_gauge* g, double kappa, double mu, int prec,
  * and returns TSM_ERR_INVALID_ARG, touching nothing, when that exceeds the
  * maximum.  The first call on a device looks up the array's device address
  * and uploads a constant table there (make it before any stream capture);
- * no call allocates device memory.  All calls share the array and it keeps
+ * no call allocates device memory.  That address is kept for the life of the
+ * process: a cudaDeviceReset after the first call is not supported.  All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU (two streams, two
  * threads) race.  Results equal tsm_contract_loops'. */
 #define TSM_CONTRACT_NOALLOC_MAX_BYTES (32 * 1024 * 1024)

@@ -269,7 +269,8 @@ struct Multi {
     TSM_CUDA(cudaMemcpyAsync(dd.p, h.data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice, s));
     const InstDesc* d = dd.as<InstDesc>();
     SolveParams prm;
-    prm.rho2 = rho * rho;
+    const double rc = cert_rho(rho, T::CERT);
+    prm.rho2 = rc * rc;
     prm.delta2 = delta() * delta();
     prm.inv_ncomp = 0.0;  // per instance
     prm.max_iter = max_iter;

@@ -43,6 +43,27 @@ int DevBuf::reserve(size_t n) {
   return TSM_OK;
 }
 
+int UseOrder::enter(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TSM_CUDA(cudaStreamIsCapturing(st, &cs));
+  capturing = (cs != cudaStreamCaptureStatusNone);
+  if (capturing) return TSM_OK;
+  if (!done) TSM_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+  TSM_CUDA(cudaStreamWaitEvent(st, done, 0));
+  return TSM_OK;
+}
+
+int UseOrder::leave(cudaStream_t st) {
+  if (capturing || !done) return TSM_OK;
+  TSM_CUDA(cudaEventRecord(done, st));
+  return TSM_OK;
+}
+
+int UseOrder::wait_host() {
+  if (done) TSM_CUDA(cudaEventSynchronize(done));
+  return TSM_OK;
+}
+
 int momentum_table(int p2max, std::vector<int>& out) {
   out.clear();
   if (p2max < 0) return -1;

@@ -10,17 +10,25 @@
 //                W^k = U_mu(x) chi^k(x+mu) - U_mu(x-mu)^dag chi^k(x-mu)
 //
 // (the four terms of the symmetric covariant insertion collapse into two
-// outer products because U commutes with g5), i.e. 10 x 16 = 160 complex
-// fields per site, summed over the sources of the batch.  These fields are
-// projected to momenta with a separable transform, x then y inside a
-// (z, t)-plane block (FP32, short sums), and z in FP64 by a second kernel,
-// which also forms every Gamma insertion from the projected 4x4 matrix
+// outer products because U commutes with g5), summed over the sources of
+// the batch.  Each Gamma insertion is formed from the 4x4 matrix at the site
 // ("by transposition and multiplication", Sec. 2.2):
-//   L_g = pref_k sum_ab Gamma_g[a][b] D[a][b],   pref_0 = -2 i mu', pref_1 = 2.
-// Gamma_g is a monomial matrix in the chiral basis, so each L_g is 4 terms.
+//   T_g = sum_ab Gamma_g[a][b] D[a][b],
+// a monomial matrix in the chiral basis, so 4 terms per insertion, giving
+// 10 x 16 = 160 complex fields per site.  (Forming the insertions after the
+// projection instead, as the paper's double-precision code could, makes the
+// FP32 sums over sites carry the large diagonal entries of D whose
+// combination cancels -- g5 has +1 and -1 on the diagonal -- and costs the
+// FP32 contraction a decade of relative accuracy on those insertions.)
+// These fields are projected to momenta with a separable transform, x then y
+// inside a (z, t)-plane block (FP32, short sums), and z in FP64 by a second
+// kernel, which also applies the derivative shift and the flavour
+// prefactors, pref_0 = -2 i mu', pref_1 = 2.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
+#include <utility>
 #include <vector>
 
 #include "dslash.cuh"
@@ -34,6 +42,61 @@ struct GammaTable {
   double re[16][4], im[16][4];
 };
 __constant__ GammaTable c_gamma;
+
+// The same insertion matrices as compile-time monomials: Gamma_g has one
+// non-zero per row a, the power i^ph[a] at column col[a].  The site-field
+// kernels form the insertion traces with them per site (before any sum over
+// sites), so that no FP32 sum ever combines the large, nearly cancelling
+// diagonal entries of the open Dirac matrices; the host table above is
+// checked against these at upload.
+struct Mono4 {
+  int col[4];
+  int ph[4];
+};
+constexpr Mono4 mono_mul(const Mono4& a, const Mono4& b) {
+  Mono4 c{};
+  for (int r = 0; r < 4; ++r) {
+    c.col[r] = b.col[a.col[r]];
+    c.ph[r] = (a.ph[r] + b.ph[a.col[r]]) & 3;
+  }
+  return c;
+}
+// chiral basis of include/tsm.h, read off row by row:
+//   g_x: (0,3) -i, (1,2) -i, (2,1) i, (3,0) i     g_y: (0,3) -1, (1,2) 1, (2,1) 1, (3,0) -1
+//   g_z: (0,2) -i, (1,3) i, (2,0) i, (3,1) -i     g_t: (0,2) 1, (1,3) 1, (2,0) 1, (3,1) 1
+constexpr Mono4 gamma_base(int mu) {
+  return mu == 0   ? Mono4{{3, 2, 1, 0}, {3, 3, 1, 1}}
+         : mu == 1 ? Mono4{{3, 2, 1, 0}, {2, 0, 0, 2}}
+         : mu == 2 ? Mono4{{2, 3, 0, 1}, {3, 1, 1, 3}}
+                   : Mono4{{2, 3, 0, 1}, {0, 0, 0, 0}};
+}
+// Gamma_g = g_x^{b0} g_y^{b1} g_z^{b2} g_t^{b3}
+constexpr Mono4 gamma_ins(int g) {
+  Mono4 m{{0, 1, 2, 3}, {0, 0, 0, 0}};
+  for (int bit = 0; bit < 4; ++bit)
+    if ((g >> bit) & 1) m = mono_mul(m, gamma_base(bit));
+  return m;
+}
+
+template <int PH, typename R>
+__device__ __forceinline__ cplx<R> times_ipow(cplx<R> z) {
+  return PH == 0 ? z : (PH == 1 ? mk<R>(-z.im, z.re) : (PH == 2 ? mk<R>(-z.re, -z.im) : mk<R>(z.im, -z.re)));
+}
+// sum_a Gamma_g[a][col_a] rowfac(a) m[a][col_a], rowfac = +scale for a < 2 (the g5 of phi = g5 s), -scale else
+template <int G, typename R>
+__device__ __forceinline__ cplx<R> insertion_trace(const cplx<R> (&m)[16], R scale) {
+  constexpr Mono4 q = gamma_ins(G);
+  cplx<R> t = scale * times_ipow<q.ph[0]>(m[0 * 4 + q.col[0]]);
+  t = t + scale * times_ipow<q.ph[1]>(m[1 * 4 + q.col[1]]);
+  t = t - scale * times_ipow<q.ph[2]>(m[2 * 4 + q.col[2]]);
+  t = t - scale * times_ipow<q.ph[3]>(m[3 * 4 + q.col[3]]);
+  return t;
+}
+template <typename R, int... G>
+__device__ __forceinline__ void store_traces(cplx<R>* out, size_t V, const cplx<R> (&m)[16], R scale,
+                                             std::integer_sequence<int, G...>) {
+  ((out[(size_t)G * V] = insertion_trace<G>(m, scale)), ...);
+}
 
 namespace {
 
@@ -102,6 +165,26 @@ int build_gamma_table(GammaTable& t) {
       if (nz != 1) return fail(TSM_ERR_CUDA, "gamma table: Gamma_%d row %d is not monomial", idx, a);
     }
   }
+  return TSM_OK;
+}
+
+// Build the table and copy it to c_gamma on stream st, waiting for the copy:
+// the copy is ordered on the caller's stream rather than on the legacy
+// default stream, which would synchronise implicitly with (and so
+// invalidate) a graph capture on a blocking stream of another host thread.
+int upload_gamma_table(cudaStream_t st) {
+  GammaTable t;  // lives until the copy has completed (synchronised below)
+  TSM_TRY(build_gamma_table(t));
+  for (int g = 0; g < 16; ++g) {
+    const Mono4 q = gamma_ins(g);
+    for (int a = 0; a < 4; ++a) {
+      const double pr[4] = {1, 0, -1, 0}, pi[4] = {0, 1, 0, -1};
+      if (t.col[g][a] != q.col[a] || t.re[g][a] != pr[q.ph[a]] || t.im[g][a] != pi[q.ph[a]])
+        return fail(TSM_ERR_CUDA, "insertion table mismatch at Gamma_%d row %d", g, a);
+    }
+  }
+  TSM_CUDA(cudaMemcpyToSymbolAsync(c_gamma, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st));
+  TSM_CUDA(cudaStreamSynchronize(st));
   return TSM_OK;
 }
 
@@ -209,12 +292,8 @@ __global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) contract_field
     scale = (R)0.25;
   }
   cplx<R>* out = a.F + (size_t)pass * NF * V + i;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const R ga = (k < 8) ? scale : -scale;  // row a = k / 4: g5 = +1 for a < 2
-    out[(size_t)k * V] = ga * m0[k];
-    out[(size_t)(16 + k) * V] = ga * m1[k];
-  }
+  store_traces(out, V, m0, scale, std::make_integer_sequence<int, 16>{});
+  store_traces(out + 16 * V, V, m1, scale, std::make_integer_sequence<int, 16>{});
 }
 
 // The same site fields with FP32 sums in packed pairs (two-wide FP32 FMA):
@@ -365,12 +444,8 @@ __global__ void __launch_bounds__(FLD_BS, 3) contract_fields_pairs_kernel(FieldA
       }
   }
   cplx<float>* out = a.F + (size_t)pass * NF * V + i;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float ga = (k < 8) ? scale : -scale;  // row a = k / 4: g5 = +1 for a < 2
-    out[(size_t)k * V] = ga * m0[k];
-    out[(size_t)(16 + k) * V] = ga * m1[k];
-  }
+  store_traces(out, V, m0, scale, std::make_integer_sequence<int, 16>{});
+  store_traces(out + 16 * V, V, m1, scale, std::make_integer_sequence<int, 16>{});
 }
 
 __device__ __forceinline__ void twiddle(cplx<float>& o, int m, int L) {
@@ -513,19 +588,11 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
     zs[q] = make_double2(re, im);
   }
   __syncthreads();
-  // prefactor: k = 0 -> -2 i mu', k = 1 -> 2
+  // prefactor: k = 0 -> -2 i mu', k = 1 -> 2 (the fields are the insertion traces already)
   const double pre = (k == 0) ? 0.0 : 2.0, pim = (k == 0) ? -2.0 * mup : 0.0;
   for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
     const int m = q / 16, gi = q % 16;
-    double re = 0.0, im = 0.0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int b = c_gamma.col[gi][a];
-      const double gr = c_gamma.re[gi][a], gm = c_gamma.im[gi][a];
-      const double2 d = zs[m * 16 + 4 * a + b];
-      re += gr * d.x - gm * d.y;
-      im += gr * d.y + gm * d.x;
-    }
+    const double re = zs[m * 16 + gi].x, im = zs[m * 16 + gi].y;
     const double lr = pre * re - pim * im, li = pre * im + pim * re;
     const int ins = 80 * k + (pass == 0 ? gi : 16 + 16 * (pass - 1) + gi);
     double* o = out + (((size_t)ins * n_mom + m) * lt + t) * 2;
@@ -846,7 +913,8 @@ void hpe_exact(double kappa, double mu, HostCplx out[160]) {
 }  // namespace
 
 struct ContractWorkspace {
-  std::mutex mu;  // held for a whole contraction
+  std::mutex mu;  // held while a contraction enqueues its work
+  UseOrder order;  // orders the GPU use across the callers' streams
   DevBuf v, fields, part, mom, aux, hpe;
 };
 
@@ -911,6 +979,38 @@ int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsr
 
 }  // namespace
 
+int prepare_contract(tsm_gauge* g, int prec, int nsrc, int n_mom, const int* mom_host, int slot, cudaStream_t st) {
+  if (slot < 0 || slot > 1 || nsrc < 1) return fail(TSM_ERR_INVALID_ARG, "prepare_contract: slot %d, nsrc %d", slot, nsrc);
+  if (prec != TSM_F32 && prec != TSM_F64) return fail(TSM_ERR_INVALID_ARG, "contraction precision %d", prec);
+  int rad = 0;
+  for (int m = 0; m < 3 * n_mom; ++m) rad = std::max(rad, std::abs(mom_host[m]));
+  if (rad > 8) return fail(TSM_ERR_INVALID_ARG, "momentum component outside [-8, 8]");
+  ContractWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    if (!g->contract_ws[slot]) g->contract_ws[slot].reset(new ContractWorkspace());
+    wp = g->contract_ws[slot].get();
+    if (!g->gamma_ready) {
+      TSM_TRY(upload_gamma_table(st));
+      g->gamma_ready = true;
+    }
+  }
+  ContractWorkspace& w = *wp;
+  {
+    std::lock_guard<std::mutex> wlock(w.mu);
+    const int V = g->geom.V, nx = 2 * rad + 1;
+    const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
+    TSM_TRY(w.order.enter(st));
+    TSM_TRY(w.v.reserve((size_t)nsrc * spinor_chunks(prec) * V * 16));
+    TSM_TRY(w.fields.reserve((size_t)160 * V * cs));
+    TSM_TRY(w.part.reserve((size_t)g->geom.L[2] * g->geom.L[3] * 160 * nx * nx * sizeof(double2)));
+    TSM_TRY(w.mom.reserve(sizeof(int) * 3 * (size_t)std::max(n_mom, 1)));
+    TSM_TRY(w.order.leave(st));
+  }
+  int nr = 1;
+  return tuned_nr(g, prec, prec, nsrc, st, &nr);
+}
+
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                    const int* mom_host, double* out_dev, int accumulate, cudaStream_t st, int slot) {
   if (slot < 0 || slot > 1) return fail(TSM_ERR_INVALID_ARG, "workspace slot %d", slot);
@@ -930,14 +1030,13 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
     if (!g->contract_ws[slot]) g->contract_ws[slot].reset(new ContractWorkspace());
     wp = g->contract_ws[slot].get();
     if (!g->gamma_ready) {
-      GammaTable t;
-      TSM_TRY(build_gamma_table(t));
-      TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+      TSM_TRY(upload_gamma_table(st));
       g->gamma_ready = true;
     }
   }
   ContractWorkspace& w = *wp;
   std::lock_guard<std::mutex> wlock(w.mu);
+  TSM_TRY(w.order.enter(st));
   const int V = g->geom.V;
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2], lt = g->geom.L[3];
@@ -988,20 +1087,18 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
     snprintf(name, sizeof(name), "contract_project_z");
     prof_add(name, ev_z.seconds(), part_bytes + out_bytes, 8.0 * 160.0 * n_mom * lt * lz + 8.0 * 160 * n_mom * lt);
   }
-  return TSM_OK;
+  return w.order.leave(st);
 }
 
 
 namespace {
 
-int contract_ws_slot(tsm_gauge* g, int slot, ContractWorkspace** out) {
+int contract_ws_slot(tsm_gauge* g, int slot, ContractWorkspace** out, cudaStream_t st) {
   std::lock_guard<std::mutex> lock(g->mu);
   if (!g->contract_ws[slot]) g->contract_ws[slot].reset(new ContractWorkspace());
   *out = g->contract_ws[slot].get();
   if (!g->gamma_ready) {
-    GammaTable t;
-    TSM_TRY(build_gamma_table(t));
-    TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+    TSM_TRY(upload_gamma_table(st));
     g->gamma_ready = true;
   }
   return TSM_OK;
@@ -1051,9 +1148,11 @@ int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev
   int rad = 0;
   TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad, mneg));
   ContractWorkspace* wp;
-  TSM_TRY(contract_ws_slot(g, 0, &wp));
+  TSM_TRY(contract_ws_slot(g, 0, &wp, st));
   std::lock_guard<std::mutex> wlock(wp->mu);
-  return tdil_body(g, *wp, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, out_dev, accumulate, st);
+  TSM_TRY(wp->order.enter(st));
+  TSM_TRY(tdil_body(g, *wp, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, out_dev, accumulate, st));
+  return wp->order.leave(st);
 }
 
 namespace {
@@ -1121,9 +1220,10 @@ int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_
   HostCplx ex[160];
   hpe_exact(kappa, mu, ex);
   ContractWorkspace* wp;
-  TSM_TRY(contract_ws_slot(g, 0, &wp));
+  TSM_TRY(contract_ws_slot(g, 0, &wp, st));
   ContractWorkspace& w = *wp;
   std::lock_guard<std::mutex> wlock(w.mu);
+  TSM_TRY(w.order.enter(st));
   const size_t fs = (size_t)nsrc * spinor_chunks(prec) * g->geom.V * 16;
   const size_t n_out = (size_t)160 * n_mom * lt * 2;
   const size_t bytes = 2 * fs + 2 * n_out * sizeof(double) + 160 * sizeof(double2) + (size_t)lt * sizeof(int);
@@ -1154,7 +1254,7 @@ int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_
   hpe_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(tmp_a, tmp_b, ex_dev, cnt_dev, vs, m0, n_mom, lt,
                                                                  out_dev, accumulate);
   TSM_CUDA(cudaGetLastError());
-  return TSM_OK;  // pageable sources of the copies above are staged before the calls return
+  return w.order.leave(st);  // pageable sources of the copies above are staged before the calls return
 }
 }  // namespace tsm
 
@@ -1180,16 +1280,14 @@ size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 // Host-side address of the scratch array on `dev` (which must be current);
 // looked up, together with the Gamma table upload, on the first call per device.
-int noalloc_setup(int dev, unsigned char** out) {
+int noalloc_setup(int dev, unsigned char** out, cudaStream_t st) {
   if (dev < 0 || dev >= kMaxDevices) return fail(TSM_ERR_INVALID_ARG, "device %d out of range", dev);
   std::lock_guard<std::mutex> l(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_contract_scratch);
     if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
-    GammaTable t;
-    TSM_TRY(build_gamma_table(t));
-    TSM_CUDA(cudaMemcpyToSymbol(c_gamma, &t, sizeof(t)));
+    TSM_TRY(upload_gamma_table(st));
     g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
   }
   *out = g_noalloc_ptr[dev];
@@ -1225,7 +1323,7 @@ int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, cons
                 "tsm_contract_loops",
                 need, v_bytes, f_bytes, part_bytes, (int)TSM_CONTRACT_NOALLOC_MAX_BYTES);
   unsigned char* base = nullptr;
-  TSM_TRY(noalloc_setup(g->ctx->device, &base));
+  TSM_TRY(noalloc_setup(g->ctx->device, &base, st));
   int* mom_dev = reinterpret_cast<int*>(base);
   void* v_dev = base + mom_bytes;
   void* f_dev = base + mom_bytes + v_bytes;

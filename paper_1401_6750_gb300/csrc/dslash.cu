@@ -137,9 +137,11 @@ int dslash_apply_mixed(tsm_gauge* g, int pf, int pl, int op, double kappa, doubl
     case TSM_OP_MDAG: return dispatch_store<+1>(g, pf, pl, kappa, -mup, in, out, nrhs, gamma5, s);
     case TSM_OP_MDAGM: {
       const size_t bytes = (size_t)nrhs * spinor_chunks(pf) * (size_t)g->geom.V * 16;
-      TSM_TRY(g->tmp.reserve(bytes));
-      TSM_TRY(dispatch_store<-1>(g, pf, pl, kappa, mup, in, g->tmp.p, nrhs, 0, s));
-      return dispatch_store<+1>(g, pf, pl, kappa, -mup, g->tmp.p, out, nrhs, gamma5, s);
+      ScratchLease lease(g->tmp);
+      TSM_TRY(lease.acquire(bytes, s));
+      TSM_TRY(dispatch_store<-1>(g, pf, pl, kappa, mup, in, lease.ptr(), nrhs, 0, s));
+      TSM_TRY(dispatch_store<+1>(g, pf, pl, kappa, -mup, lease.ptr(), out, nrhs, gamma5, s));
+      return lease.release(s);
     }
   }
   return fail(TSM_ERR_INVALID_ARG, "unknown operator %d", op);

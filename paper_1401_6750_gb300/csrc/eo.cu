@@ -83,6 +83,7 @@ __global__ void k_diag(void* out, const void* in, double cr, double ci, int vh) 
 
 struct EoWorkspace {
   std::mutex mu;  // held for a whole solve
+  UseOrder order;  // orders the GPU use across the callers' streams
   int cap = 0, nblk = 0;
   DevBuf st, partial, counter, mask, b, t1, tep, eta_e, x, r, p, q, tes, xacc, full;
   RhsState* h_st = nullptr;
@@ -134,7 +135,7 @@ struct SolverEO {
 
   static size_t half(int prec, int V, int n) { return (size_t)n * spinor_chunks(prec) * (size_t)(V / 2) * 16; }
 
-  static int reserve(tsm_gauge* g, EoWorkspace& w, int nrhs) {
+  static int reserve(tsm_gauge* g, EoWorkspace& w, int nrhs, cudaStream_t s) {
     if (w.cap >= nrhs) return TSM_OK;
     for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
     w.graphs.clear();
@@ -143,7 +144,7 @@ struct SolverEO {
     TSM_TRY(w.st.reserve(sizeof(RhsState) * nrhs));
     TSM_TRY(w.partial.reserve(sizeof(double) * (size_t)nrhs * w.nblk));
     TSM_TRY(w.counter.reserve(sizeof(unsigned) * nrhs));
-    TSM_CUDA(cudaMemset(w.counter.p, 0, sizeof(unsigned) * nrhs));
+    TSM_CUDA(cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned) * nrhs, s));  // stream-ordered (see solver.cu)
     TSM_TRY(w.mask.reserve(sizeof(int) * nrhs));
     TSM_TRY(w.b.reserve(half(T::PP, V, nrhs)));
     TSM_TRY(w.t1.reserve(half(T::PP, V, nrhs)));
@@ -204,7 +205,8 @@ struct SolverEO {
 
   static SolveParams params(const tsm_gauge* g, double rho, int max_iter) {
     SolveParams p;
-    p.rho2 = rho * rho;
+    const double rc = cert_rho(rho, T::CERT);
+    p.rho2 = rc * rc;
     p.delta2 = delta() * delta();
     p.inv_ncomp = 1.0 / (12.0 * (double)(g->geom.V / 2));
     p.max_iter = max_iter;
@@ -285,9 +287,13 @@ struct SolverEO {
     return TSM_OK;
   }
 
-  static int run_chunk(const tsm_gauge* g, EoWorkspace& w, int nrhs, double kappa, double mup, const SolveParams& prm,
-                       cudaStream_t s) {
-    const int k = eo_chunk();
+  // The graph of one chunk of iterations for (nrhs, kappa, mu'), captured on
+  // stream s if not cached.  The kernels' arguments hold only workspace
+  // pointers, kappa, mu' and solver constants; everything a solve changes
+  // (rho, max_iter, the iterates) lives in the device state, so a cached graph
+  // serves every later solve of that shape.
+  static int ensure_graph(const tsm_gauge* g, EoWorkspace& w, int nrhs, double kappa, double mup,
+                          const SolveParams& prm, cudaStream_t s, cudaGraphExec_t* out) {
     if (w.graph_kappa != kappa || w.graph_mup != mup) {
       for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
       w.graphs.clear();
@@ -296,6 +302,7 @@ struct SolverEO {
     }
     auto found = w.graphs.find(nrhs);
     if (found == w.graphs.end()) {
+      const int k = eo_chunk();
       cudaGraph_t graph;
       TSM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       for (int it = 0; it < k; ++it) iteration(g, w, nrhs, kappa, mup, prm, s);
@@ -308,9 +315,27 @@ struct SolverEO {
       if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate", __FILE__, __LINE__);
       found = w.graphs.emplace(nrhs, exec).first;
     }
-    TSM_CUDA(cudaGraphLaunch(found->second, s));
-    count_launches(5LL * k);
+    *out = found->second;
     return TSM_OK;
+  }
+
+  static int run_chunk(const tsm_gauge* g, EoWorkspace& w, int nrhs, double kappa, double mup, const SolveParams& prm,
+                       cudaStream_t s) {
+    cudaGraphExec_t exec;
+    TSM_TRY(ensure_graph(g, w, nrhs, kappa, mup, prm, s, &exec));
+    TSM_CUDA(cudaGraphLaunch(exec, s));
+    count_launches(5LL * eo_chunk());
+    return TSM_OK;
+  }
+
+  static void set_shapes(EoWorkspace& w) {
+    const int nr_s = eo_nr(T::PS), nr_p = eo_nr(T::PP);
+    if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
+      for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
+      w.graphs.clear();
+    }
+    w.nr_s = nr_s;
+    w.nr_p = nr_p;
   }
 
   // r = b - Mhat^dag Mhat x_true for the masked right-hand sides (precise operator)
@@ -348,15 +373,7 @@ struct SolverEO {
     const int V = g->geom.V;
     const size_t Vh = (size_t)V / 2;
     dim3 fg((V + EW_BS - 1) / EW_BS, nrhs), eg(((int)Vh + EW_BS - 1) / EW_BS, nrhs);
-    {
-      const int nr_s = eo_nr(T::PS), nr_p = eo_nr(T::PP);
-      if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
-        for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
-        w.graphs.clear();
-      }
-      w.nr_s = nr_s;
-      w.nr_p = nr_p;
-    }
+    set_shapes(w);
     count_launches(7);
     // split eta; t1 = eta_o, tep = M_ee^{-1} eta_e
     k_gather_eo<T::PP><<<fg, EW_BS, 0, s>>>(w.full.p, w.eta_e.p, w.t1.p, g->geom);
@@ -461,13 +478,16 @@ int solve_eo_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_ite
   }
   EoWorkspace& w = *wp;
   std::lock_guard<std::mutex> wlock(w.mu);
-  TSM_TRY(SolverEO<KIND>::reserve(g, w, nrhs));
+  TSM_TRY(w.order.enter(s));
+  TSM_TRY(SolverEO<KIND>::reserve(g, w, nrhs, s));
   if (eta) {
     TSM_TRY(spinor_convert(g, T::PP, w.full.p, eta_prec, eta, nrhs, gamma5_io, s));
   } else {
     TSM_TRY(make_sources(g, seed, first, nrhs, T::PP, w.full.p, s));
   }
-  return SolverEO<KIND>::solve(g, w, nrhs, kappa, mu, rho, max_iter, out_prec, x_out, gamma5_io, stats, s);
+  const int rc = SolverEO<KIND>::solve(g, w, nrhs, kappa, mu, rho, max_iter, out_prec, x_out, gamma5_io, stats, s);
+  const int rc_order = w.order.leave(s);
+  return rc != TSM_OK ? rc : rc_order;
 }
 
 }  // namespace
@@ -504,9 +524,9 @@ template <typename R, int P>
 int mhat_apply(tsm_gauge* g, int dag, double kappa, double mu, const void* in, void* out, int nrhs, cudaStream_t s) {
   const int V = g->geom.V;
   const size_t half = (size_t)nrhs * spinor_chunks(P) * (size_t)(V / 2) * 16;
-  std::lock_guard<std::mutex> lock(g->mu);
-  TSM_TRY(g->eo_tmp.reserve(3 * half));
-  char* base = g->eo_tmp.as<char>();
+  ScratchLease lease(g->eo_tmp);
+  TSM_TRY(lease.acquire(3 * half, s));
+  char* base = static_cast<char*>(lease.ptr());
   void *in_o = base, *t_e = base + half, *out_o = base + 2 * half;
   const double mup = 2.0 * kappa * mu;
   dim3 fg((V + EW_BS - 1) / EW_BS, nrhs);
@@ -519,7 +539,7 @@ int mhat_apply(tsm_gauge* g, int dag, double kappa, double mu, const void* in, v
   TSM_CUDA(cudaMemsetAsync(t_e, 0, half, s));  // zeros on the even sites of the result
   k_scatter_eo<P, P><<<fg, EW_BS, 0, s>>>(out, t_e, out_o, g->geom, 0);
   TSM_CUDA(cudaGetLastError());
-  return TSM_OK;
+  return lease.release(s);
 }
 
 }  // namespace
@@ -534,6 +554,44 @@ int schur_apply(tsm_gauge* g, int prec, int dag, double kappa, double mu, const 
     case TSM_BF16: return mhat_apply<float, TSM_BF16>(g, dag, kappa, mu, in, out, nrhs, s);
   }
   return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+}
+
+namespace {
+template <int KIND>
+int prepare_eo_kind(tsm_gauge* g, int nrhs, double kappa, double mu, int slot, cudaStream_t s) {
+  EoWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    auto& ws = g->eo_ws[KIND + 64 * slot];
+    if (!ws) ws.reset(new EoWorkspace());
+    wp = ws.get();
+  }
+  EoWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
+  TSM_TRY(w.order.enter(s));
+  TSM_TRY(SolverEO<KIND>::reserve(g, w, nrhs, s));
+  if (!profiling()) {  // the chunk graph too: a solve then captures nothing
+    SolverEO<KIND>::set_shapes(w);
+    cudaGraphExec_t exec;
+    TSM_TRY(SolverEO<KIND>::ensure_graph(g, w, nrhs, kappa, 2.0 * kappa * mu, SolverEO<KIND>::params(g, 0.5, 1), s,
+                                         &exec));
+  }
+  return w.order.leave(s);
+}
+}  // namespace
+
+// Workspace and chunk graph of an even-odd solve of nrhs right-hand sides at
+// (kappa, mu) on `slot`, made ahead of the solve (the checkerboarded stencils
+// are not autotuned).
+int prepare_eo(tsm_gauge* g, int solver, int nrhs, double kappa, double mu, int slot, cudaStream_t s) {
+  if (!eo_lattice(g->geom)) return fail(TSM_ERR_INVALID_ARG, "even-odd solves need even extents");
+  switch (solver & ~TSM_SOLVER_EO) {
+    case TSM_SOLVER_F64: return prepare_eo_kind<TSM_SOLVER_F64>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_F32_RELIABLE: return prepare_eo_kind<TSM_SOLVER_F32_RELIABLE>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_LP_F16: return prepare_eo_kind<TSM_SOLVER_LP_F16>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_LP_BF16: return prepare_eo_kind<TSM_SOLVER_LP_BF16>(g, nrhs, kappa, mu, slot, s);
+  }
+  return fail(TSM_ERR_INVALID_ARG, "unknown solver %d", solver);
 }
 
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,

@@ -432,7 +432,9 @@ int backward_impl(tsm_gauge* g, double kappa, double mu, const void* s_dev, int 
   if (!w.table) {
     GammaTable t;
     TSM_TRY(gamma_table(t));
-    TSM_CUDA(cudaMemcpyToSymbol(c_gamma_grad, &t, sizeof(t)));
+    // stream-ordered, not on the legacy default stream (see upload_gamma_table)
+    TSM_CUDA(cudaMemcpyToSymbolAsync(c_gamma_grad, &t, sizeof(t), 0, cudaMemcpyHostToDevice, st));
+    TSM_CUDA(cudaStreamSynchronize(st));
     w.table = true;
   }
   // which insertions carry gradient (skipped otherwise)

@@ -48,6 +48,61 @@ struct DevBuf {
   T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Orders the uses of a library-owned buffer across streams: a user's stream
+// waits (enter) for the event recorded after the previous user's last
+// launch, and records it again (leave) after its own.  Callers hold the
+// buffer's mutex from enter to leave.  Inside a stream capture both steps
+// are left out (an event recorded outside a capture cannot be waited on
+// inside it); captured calls on one handle must then be ordered by the
+// caller.
+struct UseOrder {
+  cudaEvent_t done = nullptr;
+  bool capturing = false;
+  UseOrder() = default;
+  UseOrder(const UseOrder&) = delete;
+  UseOrder& operator=(const UseOrder&) = delete;
+  ~UseOrder() {
+    if (done) cudaEventDestroy(done);
+  }
+  int enter(cudaStream_t st);
+  int leave(cudaStream_t st);
+  // host wait for the previous user's last launch (before freeing or growing)
+  int wait_host();
+};
+
+// Library-owned scratch that calls on any host thread and stream share.  A
+// call holds the lease (and so the mutex) while it enqueues the work that
+// uses the buffer, ordered as UseOrder describes.
+struct SharedScratch {
+  std::mutex mu;
+  DevBuf buf;
+  UseOrder order;
+};
+
+class ScratchLease {
+ public:
+  explicit ScratchLease(SharedScratch& s) : s_(s), lock_(s.mu) {}
+  ScratchLease(const ScratchLease&) = delete;
+  ScratchLease& operator=(const ScratchLease&) = delete;
+  // at least `bytes` of scratch, ordered after its previous use on stream st
+  int acquire(size_t bytes, cudaStream_t st) {
+    if (s_.buf.bytes < bytes || !s_.buf.p) {
+      int rc = s_.order.wait_host();  // the old buffer may still be in use
+      if (rc != 0) return rc;
+      rc = s_.buf.reserve(bytes);
+      if (rc != 0) return rc;
+    }
+    return s_.order.enter(st);
+  }
+  // record the end of this call's use on st (call after the last launch)
+  int release(cudaStream_t st) { return s_.order.leave(st); }
+  void* ptr() const { return s_.buf.p; }
+
+ private:
+  SharedScratch& s_;
+  std::lock_guard<std::mutex> lock_;
+};
+
 // Per right-hand-side solver state, resident on the device.
 struct RhsState {
   double rr;       // |r|^2 of the iterated residual
@@ -105,8 +160,8 @@ struct tsm_gauge {
   std::map<long long, std::unique_ptr<tsm::EoWorkspace, tsm::EoWsDeleter>> eo_ws;
   std::unique_ptr<tsm::ContractWorkspace, tsm::ContractWsDeleter> contract_ws[2];
   bool gamma_ready = false;  // insertion table uploaded (guarded by mu)
-  tsm::DevBuf tmp;  // operator scratch (M^dag M intermediate, conversions)
-  tsm::DevBuf eo_tmp;  // Schur operator scratch (three half-volume fields; guarded by mu)
+  tsm::SharedScratch tmp;     // operator scratch (M^dag M intermediate)
+  tsm::SharedScratch eo_tmp;  // Schur operator scratch (three half-volume fields)
   std::mutex tsm_mu;       // guards the TSM buffers
   tsm::DevBuf tsm_acc;     // TSM accumulators and estimate
   tsm::DevBuf tsm_sol;     // solutions of one batch
@@ -172,6 +227,11 @@ int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double r
                      const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
                      int gamma5_io, tsm_solve_stats* stats, cudaStream_t s, int slot = 0);
 int solver_precise_prec(int solver);
+// Workspace, autotuned launch shapes (full-lattice solvers) and iteration-chunk
+// graph of a later solve of nrhs right-hand sides at (kappa, mu) on `slot`, so
+// that the solve itself allocates, times and captures nothing (solver.cu, eo.cu)
+int prepare_solve(tsm_gauge* g, int solver, int nrhs, double kappa, double mu, int slot, cudaStream_t s);
+int prepare_eo(tsm_gauge* g, int solver, int nrhs, double kappa, double mu, int slot, cudaStream_t s);
 // The same with the even-odd preconditioned CG (solver carries TSM_SOLVER_EO; eo.cu).
 int solve_batch_eo(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,
                    const void* eta, int eta_prec, uint64_t seed, uint64_t first, int out_prec, void* x_out,
@@ -195,6 +255,8 @@ unsigned solver_link_precs(int solver);
 // ---- contraction (contract.cu)
 int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* s_dev, int nsrc, int n_mom,
                    const int* mom_host, double* out_dev, int accumulate, cudaStream_t s, int slot = 0);
+// Workspace, insertion table and tuned operator shape of a later contract_loops of nsrc sources on `slot`
+int prepare_contract(tsm_gauge* g, int prec, int nsrc, int n_mom, const int* mom_host, int slot, cudaStream_t s);
 // Standard-estimator loops of sources eta (time-diluted: t0[r] >= 0, or volume
 // sources: t0[r] = -1) and their solutions s (contract.cu)
 int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,

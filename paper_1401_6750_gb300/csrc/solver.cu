@@ -42,6 +42,7 @@ using namespace solverk;
 // ---------------------------------------------------------------- workspace
 struct SolverWorkspace {
   std::mutex mu;  // held for a whole solve
+  UseOrder order;  // orders the GPU use across the callers' streams
   int kind = -1;
   int cap = 0;  // right-hand sides allocated
   int nblk = 0;
@@ -102,7 +103,7 @@ struct Solver {
   using Rs = typename T::Rs;
   using Rp = typename T::Rp;
 
-  static int reserve(tsm_gauge* g, SolverWorkspace& w, int nrhs) {
+  static int reserve(tsm_gauge* g, SolverWorkspace& w, int nrhs, cudaStream_t s) {
     if (w.cap >= nrhs) return TSM_OK;
     for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
     w.graphs.clear();
@@ -111,7 +112,10 @@ struct Solver {
     TSM_TRY(w.st.reserve(sizeof(RhsState) * nrhs));
     TSM_TRY(w.partial.reserve(sizeof(double) * (size_t)nrhs * w.nblk));
     TSM_TRY(w.counter.reserve(sizeof(unsigned) * nrhs));
-    TSM_CUDA(cudaMemset(w.counter.p, 0, sizeof(unsigned) * nrhs));
+    // stream-ordered: a legacy-stream memset would implicitly synchronise with
+    // (and so invalidate) a graph capture running on a blocking stream of
+    // another host thread
+    TSM_CUDA(cudaMemsetAsync(w.counter.p, 0, sizeof(unsigned) * nrhs, s));
     TSM_TRY(w.mask.reserve(sizeof(int) * nrhs));
     TSM_TRY(w.b.reserve(field_bytes(T::PP, V, nrhs)));
     TSM_TRY(w.t.reserve(field_bytes(T::PP, V, nrhs)));
@@ -156,7 +160,8 @@ struct Solver {
 
   static SolveParams params(const tsm_gauge* g, double rho, int max_iter) {
     SolveParams p;
-    p.rho2 = rho * rho;
+    const double rc = cert_rho(rho, T::CERT);
+    p.rho2 = rc * rc;
     p.delta2 = delta() * delta();
     p.inv_ncomp = 1.0 / (12.0 * (double)g->geom.V);
     p.max_iter = max_iter;
@@ -228,7 +233,18 @@ struct Solver {
       TSM_CUDA(cudaGetLastError());
       return TSM_OK;
     }
-    // kernel arguments carry kappa and mu'; a change invalidates the cached graphs
+    cudaGraphExec_t exec;  // kernel arguments carry kappa and mu': a change invalidates the cached graphs
+    TSM_TRY(ensure_graph(g, w, nrhs, kappa, mup, prm, s, &exec));
+    TSM_CUDA(cudaGraphLaunch(exec, s));
+    count_launches(3LL * k);
+    return TSM_OK;
+  }
+
+  // The chunk graph for nrhs, captured on s if not cached (kernel arguments
+  // hold workspace pointers, kappa, mu' and solver constants only; what a
+  // solve changes lives in the device state).
+  static int ensure_graph(const tsm_gauge* g, SolverWorkspace& w, int nrhs, double kappa, double mup,
+                          const SolveParams& prm, cudaStream_t s, cudaGraphExec_t* out) {
     if (w.graph_kappa != kappa || w.graph_mup != mup) {
       for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
       w.graphs.clear();
@@ -237,9 +253,11 @@ struct Solver {
     }
     auto found = w.graphs.find(nrhs);
     if (found == w.graphs.end()) {
+      const int k = chunk_iterations();
       cudaGraph_t graph;
       TSM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       for (int i = 0; i < k; ++i) iteration(g, w, nrhs, kappa, mup, prm, s);
+      count_launches(-3LL * k);  // captured, not launched
       cudaError_t e = cudaStreamEndCapture(s, &graph);
       if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture", __FILE__, __LINE__);
       cudaGraphExec_t exec;
@@ -248,8 +266,21 @@ struct Solver {
       if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate", __FILE__, __LINE__);
       found = w.graphs.emplace(nrhs, exec).first;
     }
-    TSM_CUDA(cudaGraphLaunch(found->second, s));
-    count_launches(3LL * k);
+    *out = found->second;
+    return TSM_OK;
+  }
+
+  // right-hand sides per thread of both operators (autotuned); a change drops the cached graphs
+  static int set_shapes(tsm_gauge* g, SolverWorkspace& w, int nrhs, cudaStream_t s) {
+    int nr_s = 1, nr_p = 1;
+    TSM_TRY(tuned_nr(g, T::PS, T::PLs, nrhs, s, &nr_s));
+    TSM_TRY(tuned_nr(g, T::PP, T::PLp, nrhs, s, &nr_p));
+    if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
+      for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
+      w.graphs.clear();
+    }
+    w.nr_s = nr_s;
+    w.nr_p = nr_p;
     return TSM_OK;
   }
 
@@ -283,17 +314,7 @@ struct Solver {
     const double mup = 2.0 * kappa * mu;
     const SolveParams prm = params(g, rho, max_iter);
     const size_t V = (size_t)g->geom.V;
-    {
-      int nr_s = 1, nr_p = 1;
-      TSM_TRY(tuned_nr(g, T::PS, T::PLs, nrhs, s, &nr_s));
-      TSM_TRY(tuned_nr(g, T::PP, T::PLp, nrhs, s, &nr_p));
-      if (nr_s != w.nr_s) {  // captured graphs bake in the launch shape
-        for (auto& kv : w.graphs) cudaGraphExecDestroy(kv.second);
-        w.graphs.clear();
-      }
-      w.nr_s = nr_s;
-      w.nr_p = nr_p;
-    }
+    TSM_TRY(set_shapes(g, w, nrhs, s));
     dim3 eg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
     // b = M^dag eta (precise), state initialisation
     count_launches(2);
@@ -373,16 +394,56 @@ int solve_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_iter, 
   SolverWorkspace& w = *wp;
   std::lock_guard<std::mutex> wlock(w.mu);
   w.kind = KIND;
-  TSM_TRY(Solver<KIND>::reserve(g, w, nrhs));
+  TSM_TRY(w.order.enter(s));
+  TSM_TRY(Solver<KIND>::reserve(g, w, nrhs, s));
   if (eta) {
     TSM_TRY(spinor_convert(g, T::PP, w.t.p, eta_prec, eta, nrhs, gamma5_io, s));
   } else {
     TSM_TRY(make_sources(g, seed, first, nrhs, T::PP, w.t.p, s));
   }
-  return Solver<KIND>::solve(g, w, nrhs, kappa, mu, rho, max_iter, out_prec, x_out, gamma5_io, stats, s);
+  const int rc = Solver<KIND>::solve(g, w, nrhs, kappa, mu, rho, max_iter, out_prec, x_out, gamma5_io, stats, s);
+  const int rc_order = w.order.leave(s);
+  return rc != TSM_OK ? rc : rc_order;
+}
+
+// Workspace and tuned launch shapes of a solve of nrhs right-hand sides on
+// `slot`, made ahead of the solve (which then allocates and times nothing).
+template <int KIND>
+int prepare_kind(tsm_gauge* g, int nrhs, double kappa, double mu, int slot, cudaStream_t s) {
+  SolverWorkspace* wp;
+  {
+    std::lock_guard<std::mutex> lock(g->mu);
+    auto& ws = g->solver_ws[KIND + 64 * slot];
+    if (!ws) ws.reset(new SolverWorkspace());
+    wp = ws.get();
+  }
+  SolverWorkspace& w = *wp;
+  std::lock_guard<std::mutex> wlock(w.mu);
+  w.kind = KIND;
+  TSM_TRY(w.order.enter(s));
+  TSM_TRY(Solver<KIND>::reserve(g, w, nrhs, s));
+  TSM_TRY(Solver<KIND>::set_shapes(g, w, nrhs, s));
+  if (graphs_enabled() && !profiling()) {  // the chunk graph too: a solve then captures nothing
+    cudaGraphExec_t exec;
+    TSM_TRY(Solver<KIND>::ensure_graph(g, w, nrhs, kappa, 2.0 * kappa * mu, Solver<KIND>::params(g, 0.5, 1), s,
+                                       &exec));
+  }
+  return w.order.leave(s);
 }
 
 }  // namespace
+
+int prepare_solve(tsm_gauge* g, int solver, int nrhs, double kappa, double mu, int slot, cudaStream_t s) {
+  if (slot < 0 || slot > 1 || nrhs < 1) return fail(TSM_ERR_INVALID_ARG, "prepare_solve: slot %d, nrhs %d", slot, nrhs);
+  if (solver & TSM_SOLVER_EO) return prepare_eo(g, solver, nrhs, kappa, mu, slot, s);
+  switch (solver) {
+    case TSM_SOLVER_F64: return prepare_kind<TSM_SOLVER_F64>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_F32_RELIABLE: return prepare_kind<TSM_SOLVER_F32_RELIABLE>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_LP_F16: return prepare_kind<TSM_SOLVER_LP_F16>(g, nrhs, kappa, mu, slot, s);
+    case TSM_SOLVER_LP_BF16: return prepare_kind<TSM_SOLVER_LP_BF16>(g, nrhs, kappa, mu, slot, s);
+  }
+  return fail(TSM_ERR_INVALID_ARG, "unknown solver %d", solver);
+}
 
 // eta == nullptr: Z4 sources (seed, first) are generated in place.
 int solve_batch_impl(tsm_gauge* g, double kappa, double mu, int solver, double rho, int max_iter, int nrhs,

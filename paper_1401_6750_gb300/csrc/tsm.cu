@@ -84,6 +84,43 @@ int solve_and_contract(tsm_gauge* g, const tsm_params* p, int solver, double rho
   return TSM_OK;
 }
 
+// Batch sizes solve_and_contract uses for n sources in batches of `batch`.
+std::vector<int> batch_sizes(int n, int batch) {
+  std::vector<int> v;
+  if (n <= 0) return v;
+  v.push_back(std::min(batch, n));
+  if (n > batch && n % batch) v.push_back(n % batch);
+  return v;
+}
+
+// Everything the two concurrent halves of a TSM need -- solver and
+// contraction workspaces, the insertion table, the autotuned launch shapes,
+// the solvers' iteration-chunk graphs, the solution buffers -- is allocated,
+// tuned and captured here, on the calling thread, before the worker thread
+// starts.  During the concurrent phase the two threads then only enqueue
+// work and replay graphs: no device allocation, free, autotuner timing run
+// or stream capture happens on one thread while the other enqueues.
+int prepare_tsm(tsm_gauge* g, const tsm_params* p, int batch, cudaStream_t s) {
+  const int lp_op = (solver_kind(p->lp_solver) == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
+  const int hp_op = (solver_kind(p->hp_solver) == TSM_SOLVER_F64) ? TSM_F64 : TSM_F32;
+  for (int nb : batch_sizes(p->n_lp, batch)) {
+    TSM_TRY(prepare_solve(g, p->lp_solver, nb, p->kappa, p->mu, 0, s));
+    TSM_TRY(prepare_contract(g, lp_op, nb, p->n_mom, p->mom, 0, s));
+  }
+  size_t sol2 = 0;
+  for (int nb : batch_sizes(p->n_hp, batch)) {
+    TSM_TRY(prepare_solve(g, p->hp_solver, nb, p->kappa, p->mu, 1, s));
+    TSM_TRY(prepare_solve(g, p->lp_solver, nb, p->kappa, p->mu, 1, s));
+    TSM_TRY(prepare_contract(g, hp_op, nb, p->n_mom, p->mom, 1, s));
+    TSM_TRY(prepare_contract(g, lp_op, nb, p->n_mom, p->mom, 1, s));
+    sol2 = std::max(sol2, std::max(tsm_spinor_bytes(g, hp_op, nb), tsm_spinor_bytes(g, lp_op, nb)));
+  }
+  TSM_TRY(g->tsm_sol.reserve(tsm_spinor_bytes(g, lp_op, std::min(batch, p->n_lp))));
+  if (sol2) TSM_TRY(g->tsm_sol2.reserve(sol2));
+  TSM_CUDA(cudaStreamSynchronize(s));
+  return TSM_OK;
+}
+
 }  // namespace
 
 }  // namespace tsm
@@ -151,6 +188,7 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
       TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[0], cudaEventDisableTiming));
       TSM_CUDA(cudaEventCreateWithFlags(&g->aux_ev[1], cudaEventDisableTiming));
     }
+    TSM_TRY(prepare_tsm(g, p, batch, s));
     cudaStream_t s2 = g->aux_stream;
     TSM_CUDA(cudaEventRecord(g->aux_ev[0], s));  // accumulators cleared
     TSM_CUDA(cudaStreamWaitEvent(s2, g->aux_ev[0], 0));

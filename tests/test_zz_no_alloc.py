@@ -21,6 +21,7 @@ from paper_1401_6750_gb300 import abi, synth
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-6  # normwise per insertion, as for the FP32 contraction tests
+TOL_F64 = 1e-11  # as for the FP64 contraction tests
 
 
 def _call(fn, g, kappa, mu, prec, nat, nsrc, moms, out):
@@ -35,27 +36,33 @@ def _loops(out):
     return a[..., 0] + 1j * a[..., 1]
 
 
-def test_noalloc_matches_regular_entry_two_calls(ctx):
-    dims = (8, 6, 4, 8)
+@pytest.mark.parametrize("prec,tol", [(abi.TSM_F32, TOL), (abi.TSM_F64, TOL_F64)])
+def test_noalloc_matches_regular_entry_two_calls(ctx, prec, tol):
+    dims = (8, 6, 4, 8) if prec == abi.TSM_F32 else (4, 6, 4, 8)
     kappa, mu = 0.125, 0.01
-    g, _ = gauge(ctx, dims, 0.3, 7, -1, precs=(abi.TSM_F32,))
+    g, _ = gauge(ctx, dims, 0.3, 7, -1, precs=(prec,))
     lib = abi.lib()
     moms = momenta.momentum_list(9)
     shape = (abi.TSM_N_INSERTIONS, len(moms), dims[3], 2)
     for call, seed in enumerate((70, 71)):  # two calls in a row, different sources
         nsrc = 3 + call
-        s = round_to(synth.gaussian_spinor(dims, seed, nrhs=nsrc), abi.TSM_F32)
-        nat = g.pack(to_device(s), abi.TSM_F32)
+        s = round_to(synth.gaussian_spinor(dims, seed, nrhs=nsrc), prec)
+        nat = g.pack(to_device(s), prec)
         ref = torch.full(shape, np.nan, dtype=torch.float64, device="cuda")
         got = torch.full(shape, np.nan, dtype=torch.float64, device="cuda")
-        assert _call(lib.tsm_contract_loops, g, kappa, mu, abi.TSM_F32, nat, nsrc, moms, ref) == abi.TSM_OK
-        rc = _call(lib.tsm_contract_loops_noalloc, g, kappa, mu, abi.TSM_F32, nat, nsrc, moms, got)
+        assert _call(lib.tsm_contract_loops, g, kappa, mu, prec, nat, nsrc, moms, ref) == abi.TSM_OK
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        free0 = torch.cuda.mem_get_info()[0]
+        rc = _call(lib.tsm_contract_loops_noalloc, g, kappa, mu, prec, nat, nsrc, moms, got)
         assert rc == abi.TSM_OK, lib.tsm_last_error()
         torch.cuda.synchronize()
+        if call > 0:  # after the first call's one-time set-up the device's free memory is unchanged
+            assert torch.cuda.mem_get_info()[0] == free0
         a, b = _loops(got), _loops(ref)
         assert np.all(np.isfinite(a))
         for ins in range(abi.TSM_N_INSERTIONS):
-            assert np.linalg.norm(a[ins] - b[ins]) <= TOL * np.linalg.norm(b[ins]), (call, ins)
+            assert np.linalg.norm(a[ins] - b[ins]) <= tol * np.linalg.norm(b[ins]), (call, ins)
     g.close()
 
 
