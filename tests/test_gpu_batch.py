@@ -56,3 +56,39 @@ def test_uneven_batch_64_sources_each(ctx):
         assert all(x["converged"] == 1 and x["true_residual"] <= 1e-2 for x in st)
     for g in gauges:
         g.close()
+
+
+@pytest.mark.parametrize("solver", [abi.TSM_SOLVER_LP_F16, abi.TSM_SOLVER_F32_RELIABLE])
+def test_batch_residuals_recomputed_by_oracle(ctx, solver):
+    """The uneven batch's solutions meet rho by the oracle's own FP64
+    operator: every instance of the 8^4 lattice (three twisted masses) and
+    the 16^3 x 32 instance at mu = 0.006, each source's true residual
+    |M^dag eta - M^dag M x| / |M^dag eta| recomputed from the downloaded x."""
+    from oracle import dirac, lattice, philox
+    nsrc = 3 if solver == abi.TSM_SOLVER_LP_F16 else 2
+    rho = 1e-2 if solver == abi.TSM_SOLVER_LP_F16 else 1e-8
+    made = [gauge(ctx, dims, 0.3, seed, -1) for dims, seed in LATTICES[:2]]
+    inst = []
+    for (g, _), (dims, _) in zip(made, LATTICES[:2]):
+        for j, mu in enumerate(MUS):
+            inst.append({"gauge": g, "dims": dims, "kappa": 0.125, "mu": mu, "noise_seed": 1005,
+                         "first_src": 8 * j, "nsrc": nsrc})
+    res = api.solve_batch([{k: v for k, v in it.items() if k != "dims"} for it in inst], solver, rho)
+    links = {dims: lk for (_, lk), (dims, _) in zip(made, LATTICES[:2])}
+    checked = 0
+    for it, (out, st) in zip(inst, res):
+        dims = it["dims"]
+        if dims == (16, 16, 16, 32) and it["mu"] != 0.006:
+            continue
+        u = lattice.effective_links(links[dims], -1)
+        x = it["gauge"].unpack(out, api.solution_prec(solver), nsrc).cpu().numpy()
+        for k in range(nsrc):
+            eta = philox.z4_source(dims, 1005, it["first_src"] + k)
+            b = dirac.apply_Mdag(u, eta, it["kappa"], it["mu"])
+            r = b - dirac.apply_MdagM(u, x[k], it["kappa"], it["mu"])
+            res_k = np.linalg.norm(r.ravel()) / np.linalg.norm(b.ravel())
+            assert st[k]["converged"] == 1 and res_k <= rho, (dims, it["mu"], k, res_k, st[k])
+            checked += 1
+    assert checked == 4 * nsrc
+    for g, _ in made:
+        g.close()

@@ -7,7 +7,7 @@
   solution.
 * The truncated solvers with EO: the defining property -- the odd-site
   normal residual of the returned x, recomputed in FP64 by the oracle, is at
-  most rho (few-percent slack for the precise operator's own rounding) -- and
+  most rho (the solvers stop a certification margin below rho) -- and
   the error against the oracle's converged solution within cond-style bounds.
 * tsm_invert (M and M^dag) and the TSM driver accept the flag; the TSM
   estimate with FP64 | EO maps equals the oracle's TSM to 1e-9.
@@ -46,13 +46,13 @@ def test_eo_f64_follows_oracle_schur_cg(ctx, dims):
     g.close()
 
 
-@pytest.mark.parametrize("solver_kind,rho,slack", [
-    (abi.TSM_SOLVER_F32_RELIABLE, 1e-8, 1.05),
-    (abi.TSM_SOLVER_LP_F16, 1e-2, 1.10),
-    (abi.TSM_SOLVER_LP_BF16, 1e-2, 1.10),
+@pytest.mark.parametrize("solver_kind,rho", [
+    (abi.TSM_SOLVER_F32_RELIABLE, 1e-8),
+    (abi.TSM_SOLVER_LP_F16, 1e-2),
+    (abi.TSM_SOLVER_LP_BF16, 1e-2),
 ])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (8, 6, 4, 10)])
-def test_eo_truncated_solvers_meet_rho(ctx, solver_kind, rho, slack, dims):
+def test_eo_truncated_solvers_meet_rho(ctx, solver_kind, rho, dims):
     kappa, mu, seed = 0.125, 0.01, 1102
     g, links = gauge(ctx, dims, 0.3, 2, -1)
     u = lattice.effective_links(links, -1)
@@ -64,7 +64,7 @@ def test_eo_truncated_solvers_meet_rho(ctx, solver_kind, rho, slack, dims):
         assert stats[k]["converged"] == 1, stats[k]
         assert stats[k]["true_residual"] <= rho
         res = evenodd.normal_residual(u, eta, x[k], dims, kappa, mu)
-        assert res <= slack * rho, (res, stats[k])
+        assert res <= rho, (res, stats[k])
         exact, _, _ = solver.solve(u, eta, kappa, mu, 1e-12)
         assert rel_err(x[k], exact) < 1e4 * rho
     g.close()
@@ -132,7 +132,7 @@ def test_eo_tsm_lowprec(ctx):
     for r in range(n_lp, n_lp + n_hp):
         hp = hp + tsm.source_loops(u, dims, kappa, mu, seed, r, 1e-12, moms)[0]
     rel = max(np.linalg.norm(parts[1][i] - hp[i]) / np.linalg.norm(hp[i]) for i in range(hp.shape[0]))
-    assert rel < 1e-5
+    assert rel < 1e-6  # FP32 HP solves: 1e-6
     assert st["n_not_converged"] == 0
     g.close()
 

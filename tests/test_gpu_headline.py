@@ -1,0 +1,63 @@
+"""The headline configuration, 24^3 x 48 (eps 0.25, gauge seed 3,
+kappa 0.125, mu 0.005, noise seed 1003), checked against the oracle at full
+size rather than trusted from small lattices:
+
+* even-odd FP16 LP solves (the bulk of the TSM): the odd-site normal
+  residual of each returned vector, recomputed by the oracle in FP64, is at
+  most rho_LP = 1e-2;
+* an even-odd HP solve (FP32 CG, float-float reliable updates): recomputed
+  residual at most rho_HP = 1e-8;
+* the FP32 contraction of that HP solution against the oracle's FP64
+  densities and direct Fourier sums for a subset of insertions (scalar and
+  g5 of both flavour structures, two derivative insertions), all 123
+  momenta, every timeslice: 1e-6 normwise per insertion.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import gauge
+from oracle import contract, evenodd, lattice, momenta, philox
+from paper_1401_6750_gb300 import abi, api
+
+pytestmark = pytest.mark.gpu
+EO = abi.TSM_SOLVER_EO
+DIMS = (24, 24, 24, 48)
+KAPPA, MU, SEED = 0.125, 0.005, 1003
+
+
+@pytest.fixture(scope="module")
+def headline(ctx):
+    g, links = gauge(ctx, DIMS, 0.25, 3, -1, precs=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16))
+    yield g, lattice.effective_links(links, -1)
+    g.close()
+
+
+def test_headline_lp_solves_meet_rho(headline):
+    g, u = headline
+    n = 2
+    nat, st = g.solve_sources(KAPPA, MU, abi.TSM_SOLVER_LP_F16 | EO, 1e-2, SEED, 0, n, nrhs_per_launch=n)
+    x = g.unpack(nat, abi.TSM_F32, n).cpu().numpy()
+    for k in range(n):
+        res = evenodd.normal_residual(u, philox.z4_source(DIMS, SEED, k), x[k], DIMS, KAPPA, MU)
+        assert st[k]["converged"] == 1 and res <= 1e-2, (k, res, st[k])
+
+
+def test_headline_hp_solve_and_contraction(headline):
+    g, u = headline
+    src = 32  # the first correction source of a 32 + 2 source step
+    nat, st = g.solve_sources(KAPPA, MU, abi.TSM_SOLVER_F32_RELIABLE | EO, 1e-8, SEED, src, 1)
+    x = g.unpack(nat, abi.TSM_F64, 1).cpu().numpy()[0]
+    res = evenodd.normal_residual(u, philox.z4_source(DIMS, SEED, src), x, DIMS, KAPPA, MU)
+    assert st[0]["converged"] == 1 and res <= 1e-8, (res, st[0])
+    # the driver contracts HP solutions in FP32
+    s32 = g.pack(g.unpack(nat, abi.TSM_F64, 1), abi.TSM_F32)
+    moms = momenta.momentum_list(9)
+    got = api.loops_complex(g.contract(KAPPA, MU, abi.TSM_F32, s32, 1, moms))
+    xs = g.unpack(s32, abi.TSM_F32, 1).cpu().numpy()[0]
+    sel = [0, 15, 80, 95,
+           contract.insertion_index(0, True, 0, 1), contract.insertion_index(1, True, 3, 8)]
+    dens = contract.loop_densities(u, xs, KAPPA, MU, only=set(sel))
+    want = contract.project(dens[sel], DIMS, moms)
+    for k, ins in enumerate(sel):
+        err = np.linalg.norm(got[ins] - want[k]) / np.linalg.norm(want[k])
+        assert err < 1e-6, (ins, err)

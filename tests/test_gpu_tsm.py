@@ -58,7 +58,7 @@ def test_tsm_lowprec_combine_and_hp_part(ctx, lp_solver):
     hp = 0
     for r in range(n_lp, n_lp + n_hp):
         hp = hp + tsm.source_loops(u, dims, kappa, mu, seed, r, 1e-12, moms)[0]
-    assert _norm_rel(parts[1], hp) < 1e-5
+    assert _norm_rel(parts[1], hp) < 1e-6  # FP32 HP solves: 1e-6
     assert st["lp_max_true_residual"] <= 1e-2 and st["hp_max_true_residual"] <= 1e-10
     assert st["n_not_converged"] == 0
     g.close()
