@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-equal-accuracy", action="store_true")
     ap.add_argument("--no-tdil", action="store_true", help="skip the time-dilution measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 16^3x32 TSM-vs-FP64 and 32^3x64 1000+50 source workloads")
     ap.add_argument("--probe", default=None, choices=["dslash", "tsm"],
                     help="run a few launches of one kernel family for an ncu capture and exit")
     ap.add_argument("--probe-time", action="store_true", help="with --probe dslash: print event-timed GB/s")
@@ -141,81 +143,217 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-# Iterations of the oracle's CG (unpreconditioned, full lattice) to rho_LP = 1e-2
-# on the 24^3x48 workload: the same CG on the GPU (bench --precond none) takes 15.
-ORACLE_LP_ITERS = 15.0
+# ---------------------------------------------------------------- oracle timing
+# The oracle (plain numpy FP64) is timed on every host core through a pool of
+# processes started with "spawn" (never forked from a process that has touched
+# the GPU).  Each worker loads the same links, the Z4 source 0 and g5 A of it
+# once; a timed "oracle step" is one source's worth of oracle work spread over
+# the workers as tasks: `iters` applications of M^dag M (the CG's operator
+# work; the vector updates are a few percent of it and are not timed), one
+# application of A (g5 A s for the loops), and the densities and direct
+# p^2 <= 9 projection of all 160 insertions in chunks.
+_W = {}
 
 
-def cpu_baseline(dims, kappa, mu, lp_iters, n_mom_all, budget_s=20.0):
-    """The oracle as it stands, on a bounded sample of one source at full size.
-
-    Sample: oracle M^dag M applications (its CG inner step) and the oracle's
-    densities of a subset of insertions plus their direct projection, each
-    timed; one source's cost = lp_iters x t(M^dag M) + 160/n x t(densities and
-    projection of n insertions).  lp_iters is the oracle CG's iteration count
-    to rho_LP (ORACLE_LP_ITERS: the unpreconditioned CG, as the oracle runs it).
-    """
+def _oracle_init(path, dims, kappa, mu):
     import numpy as np
-    from oracle import contract, dirac, lattice, momenta, philox
-    from paper_1401_6750_gb300 import synth
-    t0 = time.time()
-    c0 = time.process_time()
-    links = synth.gauge_links(dims, 0.25, 3)
-    u = lattice.effective_links(links, -1)
-    eta = philox.z4_source(dims, 1003, 0)
-    t1 = time.time()
-    c1 = time.process_time()
-    n_app = 0
-    x = eta
-    while True:
-        x = dirac.apply_MdagM(u, x, kappa, mu)
-        n_app += 1
-        if time.time() - t1 > budget_s / 3 or n_app >= 4:
-            break
-    t_mdm = (time.time() - t1) / n_app
-    # densities of the 16 ultra-local insertions of one flavour + projection
-    moms = momenta.momentum_list(9)
-    t2 = time.time()
-    phi = dirac.gamma5(eta)
-    from oracle.gamma import INSERTIONS
-    dens = np.stack([contract.bilinear(phi, INSERTIONS[gi], eta) for gi in range(16)])
-    contract.project(dens, dims, moms)
-    t_ins = (time.time() - t2) / 16
-    per_source = lp_iters * t_mdm + 160 * t_ins * 1.0
-    # threads the timed sample actually kept busy: CPU time over wall time
-    busy = (time.process_time() - c1) / max(time.time() - t1, 1e-9)
-    cores = max(1, int(round(busy)))
-    avail = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    from oracle import dirac, lattice, momenta, philox
+    links = np.load(path, mmap_mode="r")
+    _W["u"] = lattice.effective_links(links, -1)
+    _W["dims"], _W["kappa"], _W["mu"] = tuple(dims), kappa, mu
+    _W["eta"] = philox.z4_source(tuple(dims), 1003, 0)
+    _W["v"] = dirac.gamma5(dirac.apply_A(_W["u"], _W["eta"], kappa))
+    _W["moms"] = momenta.momentum_list(9)
+
+
+def _oracle_task(task):
+    from oracle import contract, dirac, solver
+    kind = task[0]
+    t0 = time.perf_counter()
+    if kind == "mdm":
+        dirac.apply_MdagM(_W["u"], _W["eta"], _W["kappa"], _W["mu"])
+        extra = None
+    elif kind == "A":
+        dirac.apply_A(_W["u"], _W["eta"], _W["kappa"])
+        extra = None
+    elif kind == "ins":
+        ins = list(task[1])
+        dens = contract.loop_densities_pair(_W["u"], _W["eta"], _W["eta"], _W["kappa"], _W["mu"], only=set(ins),
+                                            chi1=_W["v"])
+        contract.project(dens[ins], _W["dims"], _W["moms"])
+        extra = len(ins)
+    else:  # "cg": the oracle's own CG to rho (iteration count)
+        _, iters, res = solver.solve(_W["u"], _W["eta"], _W["kappa"], _W["mu"], task[1])
+        extra = iters
+    return kind, time.perf_counter() - t0, extra
+
+
+class OraclePool:
+    """Spawned worker processes holding the oracle's inputs at full size."""
+
+    def __init__(self, dims, kappa, mu, workers=None):
+        import multiprocessing as mp
+        import tempfile
+        import numpy as np
+        from paper_1401_6750_gb300 import synth
+        avail = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        v = 1
+        for d in dims:
+            v *= d
+        # about 12 site-sized complex fields plus the 160-insertion density array per worker
+        per_worker = v * (160 * 16 + 12 * 192 + 2 * 576)
+        try:
+            mem = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        except (ValueError, OSError):
+            mem = 64 << 30
+        self.workers = max(1, min(workers or avail, avail, int(0.6 * mem // per_worker)))
+        self.cores_available = avail
+        self.tmp = tempfile.NamedTemporaryFile(suffix=".npy", delete=False)
+        self.tmp.close()
+        np.save(self.tmp.name, synth.gauge_links(dims, 0.25, 3))
+        t0 = time.perf_counter()
+        self.pool = mp.get_context("spawn").Pool(self.workers, initializer=_oracle_init,
+                                                 initargs=(self.tmp.name, list(dims), kappa, mu))
+        # wait until every worker has run its initializer
+        self.pool.map(time.sleep, [0.2] * self.workers)
+        self.setup_s = time.perf_counter() - t0
+
+    def step(self, iters):
+        """One source's worth of oracle work over all workers; wall seconds and task times."""
+        chunks = max(1, self.workers)
+        ins_chunks = [list(range(k, 160, chunks)) for k in range(chunks)]
+        tasks = [("mdm",)] * int(round(iters)) + [("A",)] + [("ins", c) for c in ins_chunks]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_task, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+        cpu = {"mdm": [], "A": [], "ins": []}
+        for kind, t, _ in res:
+            cpu[kind].append(t)
+        return wall, cpu
+
+    def cg_iterations(self, rho):
+        kind, t, iters = self.pool.apply(_oracle_task, (("cg", rho),))
+        return iters, t
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        try:
+            os.unlink(self.tmp.name)
+        except OSError:
+            pass
+
+
+def oracle_step_model(wall, cpu, iters_lp, iters_hp, n_lp, n_hp):
+    """Oracle seconds for the 32 + 2 source TSM step from one timed oracle
+    step (a source solved with iters_lp CG iterations and contracted, on all
+    workers): every source gets an LP solve and a contraction, the correction
+    sources also an HP solve (iters_hp iterations) and a second contraction."""
+    import statistics
+    t_mdm = statistics.median(cpu["mdm"])
+    t_contract = sum(cpu["A"]) + sum(cpu["ins"])
+    t_source_cpu = iters_lp * t_mdm + t_contract           # one core, under full load
+    step_cpu = (n_lp + n_hp) * t_source_cpu + n_hp * (iters_hp * t_mdm + t_contract)
+    return step_cpu, t_mdm, t_contract, t_source_cpu
+
+
+def cpu_baseline(dims, kappa, mu, iters_lp, iters_hp, n_lp, n_hp, iters_how):
+    """The oracle as it stands on all host cores: one timed oracle step (see
+    OraclePool), scaled to the bench's TSM step of n_lp + n_hp sources."""
+    pool = OraclePool(dims, kappa, mu)
+    try:
+        wall, cpu = pool.step(iters_lp)
+    finally:
+        pool.close()
+    step_cpu, t_mdm, t_contract, t_src = oracle_step_model(wall, cpu, iters_lp, iters_hp, n_lp, n_hp)
+    # the step's sources are independent: the workers process them in parallel
+    step_wall = step_cpu / pool.workers
     return {
-        "value": 1.0 / per_source, "unit": UNIT, "cores": cores, "cores_available": avail, "kind": "oracle",
-        "sample": ("oracle numpy FP64 at %s: %d M^dag M applications (%.2f s each) x %.0f LP iterations"
-                   " + 16 ultra-local insertion densities with direct p^2<=9 projection (%.2f s per insertion)"
-                   " x 160; setup %.1f s excluded" % ("x".join(map(str, dims)), n_app, t_mdm, lp_iters, t_ins,
-                                                       t1 - t0)),
+        "value": (n_lp + n_hp) / step_wall, "unit": UNIT, "cores": pool.workers,
+        "cores_available": pool.cores_available, "kind": "oracle",
+        "single_core_value": (n_lp + n_hp) / step_cpu,
+        "sample": ("oracle numpy FP64 at %s on %d spawned worker processes: one source's oracle work (%d M^dag M "
+                   "applications, %.2f s each; g5 A s and the densities with direct p^2<=9 projection of all 160 "
+                   "insertions, %.1f s in all) took %.1f s of wall time; the %d + %d source TSM step (every source "
+                   "an LP solve of %d iterations and a contraction, the %d correction sources also an HP solve of "
+                   "%d iterations and a second contraction) is that per-source work scaled, spread over the "
+                   "workers; iteration counts %s" % (
+                       "x".join(map(str, dims)), pool.workers, int(round(iters_lp)), t_mdm, t_contract, wall, n_lp,
+                       n_hp, int(round(iters_lp)), n_hp, int(round(iters_hp)), iters_how)),
+        "extrapolated": True,
     }
 
 
+def gpu_cg_iterations(dims, kappa, mu, rhos, device=0, gauge=None):
+    """Iterations of the library's FP64 full-lattice CG on M^dag M (the same
+    textbook CG and stopping rule as the oracle's: the parity tests check the
+    counts agree within one) for Z4 source 0 of noise seed 1003, at each rho."""
+    from paper_1401_6750_gb300 import abi, api, synth
+    ctx = None
+    g = gauge
+    if g is None:
+        ctx = api.Context(device)
+        g = api.Gauge(ctx, synth.gauge_links(dims, 0.25, 3), dims, -1, precisions=(abi.TSM_F64,))
+    out = []
+    for rho in rhos:
+        _, st = g.solve_sources(kappa, mu, abi.TSM_SOLVER_F64, rho, 1003, 0, 1)
+        out.append(float(st[0]["iterations"]))
+    if ctx is not None:
+        g.close()
+        ctx.close()
+    return out
+
+
 def run_reference(args):
-    """Reference arm: the FP64 oracle, timed on the host cores."""
+    """Reference arm: the FP64 oracle, timed on all host cores.  Each step is
+    one timed oracle step (one source solved with the oracle CG's own LP
+    iteration count and contracted over all 160 insertions, spread over the
+    spawned workers), scaled to the bench's 32 + 2 source TSM step."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     dims = [int(v) for v in args.dims.split(",")] if args.dims else WORKLOAD["dims"]
-    vals = []
-    for k in range(args.warmup + args.steps):
-        b = cpu_baseline(dims, WORKLOAD["kappa"], WORKLOAD["mu"], lp_iters=ORACLE_LP_ITERS, n_mom_all=123,
-                         budget_s=15.0)
-        if k >= args.warmup:
-            vals.append(b)
-    v = sorted(x["value"] for x in vals)[len(vals) // 2]
+    kappa, mu = WORKLOAD["kappa"], WORKLOAD["mu"]
+    n_lp, n_hp = args.nrhs, args.n_hp
+    # the HP count from the library's FP64 CG (an oracle CG to 1e-8 at this size runs for many minutes);
+    # the LP count from the oracle's own CG, measured below
+    iters_hp, how_hp = None, ""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            iters_hp = gpu_cg_iterations(dims, kappa, mu, [WORKLOAD["rho_hp"]])[0]
+            how_hp = "HP %d from the library's FP64 CG (same algorithm)" % iters_hp
+    except Exception as e:  # no GPU: LP-only model
+        how_hp = "no GPU for the HP count (%s): HP solves counted as LP" % type(e).__name__
+    pool = OraclePool(dims, kappa, mu)
+    try:
+        iters_lp, t_cg = pool.cg_iterations(WORKLOAD["rho_lp"])
+        if iters_hp is None:
+            iters_hp = iters_lp
+        how = "LP %d measured by the oracle's own CG (%.0f s); %s" % (iters_lp, t_cg, how_hp)
+        vals = []
+        for k in range(args.warmup + args.steps):
+            wall, cpu = pool.step(iters_lp)
+            if k >= args.warmup:
+                step_cpu, t_mdm, t_contract, _ = oracle_step_model(wall, cpu, iters_lp, iters_hp, n_lp, n_hp)
+                vals.append(((n_lp + n_hp) * pool.workers / step_cpu, wall, t_mdm, t_contract))
+    finally:
+        pool.close()
+    vals.sort()
+    v, wall, t_mdm, t_contract = vals[len(vals) // 2]
+    sample = ("each step: one source's oracle work (%d M^dag M applications, %.2f s each; g5 A s and the 160 "
+              "insertion densities with direct p^2<=9 projection, %.1f s in all) on %d spawned worker processes, "
+              "%.1f s of wall time, scaled to the %d + %d source TSM step (every source an LP solve and a "
+              "contraction, the correction sources also an HP solve and a second contraction): the value is "
+              "extrapolated from the timed pieces; iteration counts %s" % (
+                  int(round(iters_lp)), t_mdm, t_contract, pool.workers, wall, n_lp, n_hp, how))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * (n_lp + n_hp) / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(WORKLOAD, dims=dims),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                         "sample": vals[0]["sample"] + "; the oracle CG's iteration count to rho_LP at this "
-                                   "configuration (15) is taken from the same CG on the GPU"},
+        "config": dict(WORKLOAD, dims=dims, sources_per_step={"lp_bulk": n_lp, "hp_correction": n_hp}),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.workers, "cores_available": pool.cores_available,
+                         "kind": "oracle", "sample": sample, "extrapolated": True},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -350,7 +488,7 @@ def lp_variants(g, abi, torch, w, flag, hp_solver, moms, n_lp, n_hp, steps=2):
     return res
 
 
-def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs=32):
+def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, moms, n_lp=64, n_hp=8, nrhs=32):
     """TSM against the plain high-precision path at equal final loop accuracy.
 
     Per-source samples (the scalar and gamma_5 loops of both flavour
@@ -367,8 +505,14 @@ def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs
     seed = 424242
     sel = [0, 15, 80, 95]
     mom = [(0, 0, 0)]
+    all_moms = np.ascontiguousarray(np.asarray(moms, dtype=np.int32))
+    scratch_out = torch.zeros((abi.TSM_N_INSERTIONS, all_moms.shape[0], g.dims[3], 2), dtype=torch.float64,
+                              device="cuda")
 
     def per_source(solver, first, n):
+        # timed per batch: the solve and the 160-insertion contraction over all
+        # p^2 <= 9 momenta, as in the TSM step; the per-source p = 0 samples
+        # for the variances are taken afterwards, outside the timed region
         stream = torch.cuda.current_stream()
         kind = solver & ~abi.TSM_SOLVER_EO
         prec = abi.TSM_F64 if kind in (abi.TSM_SOLVER_F64, abi.TSM_SOLVER_F32_RELIABLE) else abi.TSM_F32
@@ -381,11 +525,12 @@ def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs
             e0.record(stream)
             sol, _ = g.solve_sources(w["kappa"], w["mu"], solver, w["rho_lp"] if solver == lp_solver else w["rho_hp"],
                                      seed, first + k0, m, nrhs_per_launch=m)
+            if prec == abi.TSM_F64:  # contract in FP32 like the TSM driver
+                sol = g.pack(g.unpack(sol, abi.TSM_F64, m), abi.TSM_F32)
+            g.contract(w["kappa"], w["mu"], abi.TSM_F32, sol, m, all_moms, out=scratch_out)
             e1.record(stream)
             e1.synchronize()
             t += e0.elapsed_time(e1) * 1e-3
-            if prec == abi.TSM_F64:  # contract in FP32 like the TSM driver
-                sol = g.pack(g.unpack(sol, abi.TSM_F64, m), abi.TSM_F32)
             field = g.native_bytes(abi.TSM_F32, 1)
             for j in range(m):
                 out = g.contract(w["kappa"], w["mu"], abi.TSM_F32, sol[j * field:(j + 1) * field], 1, mom)
@@ -414,7 +559,8 @@ def equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, n_lp=64, n_hp=8, nrhs
                     "speedup_at_equal_error": float(cost_plain / cost_tsm)})
     return {"samples": {"lp": n_lp, "hp": n_hp}, "t_lp_s_per_source": t_lp, "t_hp_s_per_source": t_hp,
             "plain_hp_sources_per_s": 1.0 / t_hp, "observables": out,
-            "note": "p = 0 loops summed over timeslices; variances from per-source samples"}
+            "note": "per-source times are solve + 160-insertion contraction over all p^2 <= 9 momenta, in batches "
+                    "of %d; p = 0 loops summed over timeslices; variances from per-source samples" % nrhs}
 
 
 def time_dilution(g, abi, torch, w, lp_solver, moms, reps=3):
@@ -527,6 +673,119 @@ def binary_storage(g, abi, torch, w, lp_solver, moms, nrhs, k_end=5):
             "storage_reduction": 1.0 - size / (n * per_source), "seconds_accumulate": t_acc,
             "sources_per_s": n / t_acc, "seconds_mean_any_n": t_read,
             "lp_iterations_mean": stats["lp_iterations_total"] / n}
+
+
+def _tsm_dev_call(g, abi, torch, kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp, hp, seed, moms, nrhs, parts=False):
+    """One tsm_solve_tsm_dev call, CUDA-event timed on the current stream."""
+    import ctypes
+    stream = torch.cuda.current_stream()
+    n_out = 160 * moms.shape[0] * g.dims[3] * 2
+    out = torch.empty(n_out, dtype=torch.float64, device="cuda")
+    pt = torch.empty(3 * n_out, dtype=torch.float64, device="cuda") if parts else None
+    p = abi.tsm_params(kappa, mu, n_lp, n_hp, rho_lp, rho_hp, lp, hp, seed, 20000, nrhs, moms.shape[0],
+                       moms.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    st = abi.tsm_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    abi.check(abi.lib().tsm_solve_tsm_dev(g.handle, ctypes.byref(p), ctypes.c_void_p(out.data_ptr()),
+                                          ctypes.c_void_p(pt.data_ptr()) if parts else None, ctypes.byref(st),
+                                          ctypes.c_void_p(stream.cuda_stream)), "tsm_solve_tsm_dev")
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) * 1e-3, out, pt, {f: getattr(st, f) for f, _ in st._fields_}
+
+
+def tsm_vs_plain_16x16x16x32(ctx, abi, api, torch, synth, nrhs=32):
+    """The 16^3 x 32 configuration (eps 0.3, gauge seed 2, kappa 0.125,
+    mu 0.01, noise seed 1002): a TSM of 200 FP16 LP sources (rho 1e-2) and
+    10 HP sources (FP32 CG, float-float reliable updates, rho 1e-8), all 160
+    insertions over the p^2 <= 9 momenta, against the plain FP64 GPU path
+    (every one of the 210 sources solved by the FP64 CG to 1e-8 and
+    contracted in FP64).  Both timed with CUDA events after a warm-up; the two
+    estimates of the p = 0 scalar and g5 loops (summed over timeslices) are
+    compared in units of the plain path's standard error."""
+    import numpy as np
+    dims, kappa, mu, seed = (16, 16, 16, 32), 0.125, 0.01, 1002
+    n_lp, n_hp = 200, 10
+    eo = abi.TSM_SOLVER_EO
+    lp, hp = abi.TSM_SOLVER_LP_F16 | eo, abi.TSM_SOLVER_F32_RELIABLE | eo
+    g = api.Gauge(ctx, synth.gauge_links(dims, 0.3, 2), dims, -1,
+                  precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16))
+    moms = np.ascontiguousarray(np.array(api.momentum_table(9), dtype=np.int32))
+    try:
+        _tsm_dev_call(g, abi, torch, kappa, mu, n_lp, n_hp, 1e-2, 1e-8, lp, hp, seed + 77, moms, nrhs)  # warm-up
+        t_tsm, est, _, st = _tsm_dev_call(g, abi, torch, kappa, mu, n_lp, n_hp, 1e-2, 1e-8, lp, hp, seed, moms, nrhs)
+        est = est.view(160, moms.shape[0], dims[3], 2).cpu().numpy()
+        # plain FP64 path on the same 210 sources: batched solves + FP64 contraction, timed together
+        stream = torch.cuda.current_stream()
+        n = n_lp + n_hp
+        acc = torch.zeros((160, moms.shape[0], dims[3], 2), dtype=torch.float64, device="cuda")
+        g.solve_sources(kappa, mu, abi.TSM_SOLVER_F64 | eo, 1e-8, seed + 77, 0, nrhs, nrhs_per_launch=nrhs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sols = []
+        for k0 in range(0, n, nrhs):
+            m = min(nrhs, n - k0)
+            sol, _ = g.solve_sources(kappa, mu, abi.TSM_SOLVER_F64 | eo, 1e-8, seed, k0, m, nrhs_per_launch=m)
+            g.contract(kappa, mu, abi.TSM_F64, sol, m, moms, out=acc, accumulate=k0 > 0)
+            sols.append((sol, m))
+        e1.record(stream)
+        e1.synchronize()
+        t_plain = e0.elapsed_time(e1) * 1e-3
+        plain = acc.cpu().numpy() / n
+        # per-source samples of the plain path (p = 0) for its standard error
+        field = g.native_bytes(abi.TSM_F64, 1)
+        samples = []
+        for sol, m in sols:
+            for j in range(m):
+                o = g.contract(kappa, mu, abi.TSM_F64, sol[j * field:(j + 1) * field], 1, [(0, 0, 0)]).cpu().numpy()
+                samples.append([complex(o[i, 0, :, 0].sum(), o[i, 0, :, 1].sum()) for i in (0, 15, 80, 95)])
+        samples = np.array(samples)
+        obs = []
+        for k, (i, name) in enumerate(zip((0, 15, 80, 95), ("scalar tau3", "gamma5 tau3", "scalar", "gamma5"))):
+            e_tsm = complex(est[i, 0, :, 0].sum(), est[i, 0, :, 1].sum())
+            e_plain = complex(plain[i, 0, :, 0].sum(), plain[i, 0, :, 1].sum())
+            se = np.sqrt((samples[:, k].real.var(ddof=1) + samples[:, k].imag.var(ddof=1)) / n)
+            obs.append({"observable": name, "tsm": [e_tsm.real, e_tsm.imag], "plain_f64": [e_plain.real, e_plain.imag],
+                        "diff_over_plain_stderr": abs(e_tsm - e_plain) / se if se > 0 else None})
+        return {"workload": "16x16x16x32 eps 0.3 seed 2, kappa 0.125, mu 0.01: TSM 200 FP16 LP + 10 HP sources vs "
+                            "the plain FP64 GPU path on the same 210 sources (even-odd CG, 160 insertions, "
+                            "%d momenta)" % moms.shape[0],
+                "tsm_seconds": t_tsm, "tsm_sources_per_s": n / t_tsm,
+                "plain_f64_seconds": t_plain, "plain_f64_sources_per_s": n / t_plain,
+                "speedup": t_plain / t_tsm,
+                "lp_iterations_mean": st["lp_iterations_total"] / (n_lp + n_hp),
+                "hp_iterations_mean": st["hp_iterations_total"] / n_hp,
+                "lp_max_true_residual": st["lp_max_true_residual"], "hp_max_true_residual": st["hp_max_true_residual"],
+                "observables": obs}
+    finally:
+        g.close()
+
+
+def tsm_32x32x32x64(ctx, abi, api, torch, synth, nrhs=32):
+    """Throughput of the differentiation configuration's volume, 32^3 x 64
+    (eps 0.3, gauge seed 7, kappa 0.125, mu 0.01): one TSM of 1000 FP16 LP
+    sources and 50 HP sources (FP32 CG, float-float reliable updates), all
+    160 insertions and p^2 <= 9 momenta, CUDA-event timed after a warm-up
+    call that builds the same launch shapes."""
+    import numpy as np
+    dims, kappa, mu, seed = (32, 32, 32, 64), 0.125, 0.01, 1005
+    eo = abi.TSM_SOLVER_EO
+    lp, hp = abi.TSM_SOLVER_LP_F16 | eo, abi.TSM_SOLVER_F32_RELIABLE | eo
+    g = api.Gauge(ctx, synth.gauge_links(dims, 0.3, 7), dims, -1,
+                  precisions=(abi.TSM_F64, abi.TSM_F32, abi.TSM_F16))
+    moms = np.ascontiguousarray(np.array(api.momentum_table(9), dtype=np.int32))
+    try:
+        _tsm_dev_call(g, abi, torch, kappa, mu, 40, 50, 1e-2, 1e-8, lp, hp, seed + 77, moms, nrhs)  # warm-up
+        t, _, _, st = _tsm_dev_call(g, abi, torch, kappa, mu, 1000, 50, 1e-2, 1e-8, lp, hp, seed, moms, nrhs)
+        return {"workload": "32x32x32x64 eps 0.3 seed 7, kappa 0.125, mu 0.01: TSM 1000 FP16 LP + 50 HP sources "
+                            "(even-odd CG, 160 insertions, %d momenta)" % moms.shape[0],
+                "seconds": t, "sources_per_s": 1050 / t,
+                "lp_iterations_mean": st["lp_iterations_total"] / 1050, "hp_iterations_mean": st["hp_iterations_total"] / 50,
+                "lp_max_true_residual": st["lp_max_true_residual"], "hp_max_true_residual": st["hp_max_true_residual"],
+                "n_not_converged": st["n_not_converged"]}
+    finally:
+        g.close()
 
 
 def main():
@@ -674,7 +933,7 @@ def main():
 
     eq = None
     if rank == 0 and not args.no_equal_accuracy:
-        eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver)
+        eq = equal_accuracy(g, abi, torch, w, lp_solver, hp_solver, moms)
 
     variants = None
     if rank == 0 and not args.no_tdil:
@@ -688,9 +947,17 @@ def main():
         hpe_var = hpe_variance(g, abi, torch, w, lp_solver)
         binstore = binary_storage(g, abi, torch, w, lp_solver, moms, args.nrhs)
 
+    cfg16 = cfg32 = None
+    if rank == 0 and not args.no_configs:
+        cfg16 = tsm_vs_plain_16x16x16x32(ctx, abi, api, torch, synth)
+        cfg32 = tsm_32x32x32x64(ctx, abi, api, torch, synth)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(dims, w["kappa"], w["mu"], ORACLE_LP_ITERS, n_mom)
+        it_lp, it_hp = gpu_cg_iterations(dims, w["kappa"], w["mu"], [w["rho_lp"], w["rho_hp"]], gauge=g)
+        cpu = cpu_baseline(dims, w["kappa"], w["mu"], it_lp, it_hp, args.nrhs, args.n_hp,
+                           "LP %d and HP %d from the library's FP64 full-lattice CG (the oracle's CG, the same "
+                           "algorithm and stopping rule), measured in this run" % (it_lp, it_hp))
 
     if rank == 0:
         line = {
@@ -699,7 +966,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w["workload"], "dims": dims, "eps": w["eps"], "kappa": w["kappa"], "mu": w["mu"],
                        "lp_solver": "%s storage (links r12, p, Ap), f32 x/r, rho %g" % (args.lp, w["rho_lp"]),
-                       "hp_solver": "f32 CG + f64 reliable updates, rho %g" % w["rho_hp"],
+                       "hp_solver": "f32 CG + float-float reliable updates and solution sum, rho %g" % w["rho_hp"],
                        "preconditioning": "even-odd (Schur complement on odd sites)" if flag else "none",
                        "sources_per_step": {"lp_bulk": args.nrhs, "hp_correction": args.n_hp},
                        "nrhs_per_launch": args.nrhs, "insertions": 160, "momenta": n_mom,
@@ -719,6 +986,8 @@ def main():
             "time_dilution": tdil,
             "hpe": hpe_var,
             "binary_storage": binstore,
+            "tsm_vs_plain_f64_16x16x16x32": cfg16,
+            "tsm_1000_50_32x32x32x64": cfg32,
         }
         print(json.dumps(line), flush=True)
     g.close()
