@@ -555,195 +555,6 @@ __device__ __forceinline__ void stencil_pairs(cplx<float> (&out)[NR][12], const 
     }
 }
 
-// ---------------------------------------------------------------- asynchronously staged hops
-// TSM_EO_STAGED=1 (variant builds) selects the staged form for the
-// checkerboarded hops with one right-hand side per thread.
-#ifndef TSM_EO_STAGED
-#define TSM_EO_STAGED 0
-#endif
-#ifdef TSM_LINK16_FULL
-constexpr bool kEoStaged = false;
-#else
-constexpr bool kEoStaged = TSM_EO_STAGED != 0;
-#endif
-// The checkerboarded hops with one right-hand side per thread are bound by
-// memory latency: each of the eight hops waits for its link and neighbour
-// spinor before its arithmetic can start, and the registers leave no room to
-// hold the next hop's operands early.  The staged form copies the operands of
-// hop h + 1 into shared memory with cp.async (16-byte and 8-byte copies that
-// take no registers while in flight) while hop h computes from the copy made
-// one step earlier.  Every thread writes and reads only its own slots
-// (slot k of thread t at stg[buf][k][t]: consecutive threads, consecutive
-// 16-byte words), so no barrier is needed: cp.async.wait_group orders the
-// thread's own copies.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// 16-byte slots per staged hop: link chunks (FP32: three float4 of rows 0, 1;
-// 16-bit: one uint4 and one uint2) then spinor chunks (6 for FP32, 3 for 16-bit)
-template <int PIN, int PL>
-struct StageShape {
-  static constexpr int NL = (PL == TSM_F32) ? 3 : 2;
-  static constexpr int NS = spinor_chunks(PIN);
-  static constexpr int N = NL + NS;
-};
-
-// Issue the copies of hop H (direction H / 2, backward when H is odd) of site i.
-template <int H, int PIN, int PL, bool EO>
-__device__ __forceinline__ void stage_issue(uint4 (*slot)[DSLASH_BS], const DslashArgs& a, int r, int i,
-                                            const int c[4]) {
-  constexpr int MU = H >> 1;
-  constexpr bool BACK = (H & 1) != 0;
-  using S = StageShape<PIN, PL>;
-  const size_t V = (size_t)a.g.V;
-  const size_t FS = EO ? V / 2 : V;
-  const int stride = dir_stride(a.g, MU);
-  const int n = BACK ? bwd_site(a.g, i, c, MU, stride) : fwd_site(a.g, i, c, MU, stride);
-  const int ls = BACK ? n : i;
-  const int t = threadIdx.x;
-  if constexpr (PL == TSM_F32) {
-    const float4* lp = reinterpret_cast<const float4*>(a.links) + (size_t)MU * 3 * V + ls;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) cp_async16(&slot[k][t], lp + k * V);
-  } else {
-    const uint4* la = reinterpret_cast<const uint4*>(a.links) + (size_t)MU * V + ls;
-    const uint2* lb = reinterpret_cast<const uint2*>(reinterpret_cast<const uint4*>(a.links) + 4 * V) +
-                      (size_t)MU * V + ls;
-    cp_async16(&slot[0][t], la);
-    cp_async8(&slot[1][t], lb);
-  }
-  const uint4* sp = reinterpret_cast<const uint4*>(a.in) + (size_t)r * S::NS * FS + (EO ? (n >> 1) : n);
-#pragma unroll
-  for (int k = 0; k < S::NS; ++k) cp_async16(&slot[S::NL + k][t], sp + k * FS);
-}
-
-// Hop H of the staged stencil from the slots: rebuild the link, project the
-// neighbour spinor and accumulate (1 +- g_mu) W h as hop_pairs does.
-template <int H, int SF, int PIN, int PL>
-__device__ __forceinline__ void stage_compute(float2 (&up)[6], float2 (&lo)[6], const uint4 (*slot)[DSLASH_BS],
-                                              const DslashArgs& a, const int c[4]) {
-  constexpr int MU = H >> 1;
-  constexpr bool BACK = (H & 1) != 0;
-  constexpr int S = BACK ? -SF : SF;
-  using SS = StageShape<PIN, PL>;
-  const int t = threadIdx.x;
-  cplx<float> u[3][3];
-  if constexpr (PL == TSM_F32) {
-    const float4 x = *reinterpret_cast<const float4*>(&slot[0][t]);
-    const float4 y = *reinterpret_cast<const float4*>(&slot[1][t]);
-    const float4 z = *reinterpret_cast<const float4*>(&slot[2][t]);
-    u[0][0] = mk<float>(x.x, x.y);
-    u[0][1] = mk<float>(x.z, x.w);
-    u[0][2] = mk<float>(y.x, y.y);
-    u[1][0] = mk<float>(y.z, y.w);
-    u[1][1] = mk<float>(z.x, z.y);
-    u[1][2] = mk<float>(z.z, z.w);
-  } else {
-    constexpr bool BF = (PL == TSM_BF16);
-    const uint4 x = slot[0][t];
-    const uint2 y = *reinterpret_cast<const uint2*>(&slot[1][t]);
-    float2 f;
-    f = Link16IO<BF>::cvt(x.x); u[0][0] = mk<float>(f.x, f.y);
-    f = Link16IO<BF>::cvt(x.y); u[0][1] = mk<float>(f.x, f.y);
-    f = Link16IO<BF>::cvt(x.z); u[0][2] = mk<float>(f.x, f.y);
-    f = Link16IO<BF>::cvt(x.w); u[1][0] = mk<float>(f.x, f.y);
-    f = Link16IO<BF>::cvt(y.x); u[1][1] = mk<float>(f.x, f.y);
-    f = Link16IO<BF>::cvt(y.y); u[1][2] = mk<float>(f.x, f.y);
-  }
-  reconstruct_row2(u);
-  cplx<float> h0[3], h1[3];
-  if constexpr (PIN == TSM_F32) {
-    cplx<float> p[12];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const float4 d = *reinterpret_cast<const float4*>(&slot[SS::NL + k][t]);
-      p[2 * k] = mk<float>(d.x, d.y);
-      p[2 * k + 1] = mk<float>(d.z, d.w);
-    }
-    auto add = [](cplx<float> x, cplx<float> y) { return x + y; };
-    auto sub = [](cplx<float> x, cplx<float> y) { return x - y; };
-    auto muli = [](cplx<float> x) { return times_i(x); };
-#pragma unroll
-    for (int col = 0; col < 3; ++col)
-      project_pair<MU, S>(h0[col], h1[col], p[col], p[3 + col], p[6 + col], p[9 + col], add, sub, muli);
-  } else {
-    constexpr bool BF = (PIN == TSM_BF16);
-    using P2 = Packed2<BF>;
-    const uint4 x = slot[SS::NL][t], y = slot[SS::NL + 1][t], z = slot[SS::NL + 2][t];
-    const uint32_t w[12] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w, z.x, z.y, z.z, z.w};
-    auto add = [](uint32_t p, uint32_t q) { return P2::add(p, q); };
-    auto sub = [](uint32_t p, uint32_t q) { return P2::sub(p, q); };
-    auto muli = [](uint32_t p) { return P2::muli(p); };
-#pragma unroll
-    for (int col = 0; col < 3; ++col) {
-      uint32_t q0, q1;
-      project_pair<MU, S>(q0, q1, w[col], w[3 + col], w[6 + col], w[9 + col], add, sub, muli);
-      const float2 f0 = P2::widen(q0), f1 = P2::widen(q1);
-      h0[col] = mk<float>(f0.x, f0.y);
-      h1[col] = mk<float>(f1.x, f1.y);
-    }
-  }
-  float sgn = 1.0f;
-  if (MU == 3) sgn = ((BACK ? c[3] == 0 : c[3] == a.g.L[3] - 1) ? (float)a.g.bc : 1.0f);
-  hop_pairs<MU, S, BACK, H == 0>(up, lo, h0, h1, u, sgn);
-  if (H == 3) {  // x and y leave the lower spins in (3, 2) order (see stencil_pairs)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) lo[k] = make_float2(lo[k].y, lo[k].x);
-  }
-}
-
-// One step of the pipeline: issue hop H + 1, wait for hop H, compute it.
-template <int H, int SF, int PIN, int PL, bool EO>
-__device__ __forceinline__ void stage_step(float2 (&up)[6], float2 (&lo)[6],
-                                           uint4 (*stg)[StageShape<PIN, PL>::N][DSLASH_BS], const DslashArgs& a,
-                                           int r, int i, const int c[4]) {
-  if constexpr (H + 1 < 8) {
-    stage_issue<H + 1, PIN, PL, EO>(stg[(H + 1) & 1], a, r, i, c);
-    cp_async_commit();
-    cp_async_wait<1>();
-  } else {
-    cp_async_wait<0>();
-  }
-  stage_compute<H, SF, PIN, PL>(up, lo, stg[H & 1], a, c);
-}
-
-template <int SF, int PIN, int PL, bool EO, int... H>
-__device__ __forceinline__ void stage_all(float2 (&up)[6], float2 (&lo)[6],
-                                          uint4 (*stg)[StageShape<PIN, PL>::N][DSLASH_BS], const DslashArgs& a,
-                                          int r, int i, const int c[4], std::integer_sequence<int, H...>) {
-  (stage_step<H, SF, PIN, PL, EO>(up, lo, stg, a, r, i, c), ...);
-}
-
-// The eight hops of site i for right-hand side r through the staging
-// pipeline; out receives the hop sum in component order (as stencil_pairs).
-template <int SF, int PIN, int PL, bool EO>
-__device__ __forceinline__ void stencil_staged(cplx<float> (&out)[12], const DslashArgs& a, int r, int i,
-                                               const int c[4]) {
-  __shared__ uint4 stg[2][StageShape<PIN, PL>::N][DSLASH_BS];
-  float2 up[6], lo[6];
-  stage_issue<0, PIN, PL, EO>(stg[0], a, r, i, c);
-  cp_async_commit();
-  stage_all<SF, PIN, PL, EO>(up, lo, stg, a, r, i, c, std::make_integer_sequence<int, 8>{});
-#pragma unroll
-  for (int col = 0; col < 3; ++col) {
-    out[col] = mk<float>(up[col].x, up[3 + col].x);
-    out[3 + col] = mk<float>(up[col].y, up[3 + col].y);
-    out[6 + col] = mk<float>(lo[col].x, lo[3 + col].x);
-    out[9 + col] = mk<float>(lo[col].y, lo[3 + col].y);
-  }
-}
-
 // Full operator at site i for NR right-hand sides: out = in + i tw g5 in - kappa * hop.
 template <int SF, typename R, int PIN, int PL, int NR, bool P2 = std::is_same<R, float>::value>
 __device__ __forceinline__ void apply_site(cplx<R> (&out)[NR][12], const DslashArgs& a, int r0, const bool (&act)[NR],
@@ -896,11 +707,7 @@ __device__ __forceinline__ void apply_site_eo(cplx<R> (&out)[NR][12], const Dsla
   int c[4];
   const int i = eo_site(a.g, j, a.parity, c);
   if constexpr (P2 && std::is_same<R, float>::value) {
-    if constexpr (kEoStaged && NR == 1 && PIN == PL) {
-      stencil_staged<SF, PIN, PL, true>(out[0], a, r0, i, c);
-    } else {
-      stencil_pairs<SF, PIN, PL, NR, true>(out, a, r0, act, i, c);
-    }
+    stencil_pairs<SF, PIN, PL, NR, true>(out, a, r0, act, i, c);
   } else {
 #pragma unroll
     for (int q = 0; q < NR; ++q)

@@ -15,6 +15,7 @@
 """
 import numpy as np
 import pytest
+import torch
 
 from conftest import rel_err
 from gpu_helpers import gauge, to_device
@@ -148,4 +149,22 @@ def test_eo_argument_checks(ctx):
     inst = dict(gauge=g, kappa=0.125, mu=0.01, noise_seed=1, first_src=0, nsrc=1)
     with pytest.raises(abi.TsmError):
         api.solve_batch([inst], abi.TSM_SOLVER_F64 | EO, 1e-8)
+    g.close()
+
+
+@pytest.mark.parametrize("solver_kind", [abi.TSM_SOLVER_LP_F16, abi.TSM_SOLVER_LP_BF16, abi.TSM_SOLVER_F32_RELIABLE])
+def test_eo_map_independent_of_batch(ctx, solver_kind):
+    """Each source's solution is the same bits whatever batch it is solved in
+    (alone, in a partial group of the shared-link hop, in groups of 8): the
+    truncated solver method needs one LP map for bulk and correction sources."""
+    dims = (6, 4, 4, 8)
+    g, _ = gauge(ctx, dims, 0.3, 4, -1)
+    prec = api.solution_prec(solver_kind)
+    rho = 1e-2 if solver_kind != abi.TSM_SOLVER_F32_RELIABLE else 1e-8
+    fs = g.native_bytes(prec, 1)
+    ref = [g.solve_sources(0.125, 0.01, solver_kind | EO, rho, 1106, k, 1)[0] for k in range(13)]
+    for nb in (3, 8, 13):
+        sol, _ = g.solve_sources(0.125, 0.01, solver_kind | EO, rho, 1106, 0, 13, nrhs_per_launch=nb)
+        for k in range(13):
+            assert torch.equal(sol[k * fs:(k + 1) * fs], ref[k]), (nb, k)
     g.close()
