@@ -928,6 +928,16 @@ def main():
     kernels = [{"name": d["name"], "launches": d["launches"], "share": round(d["seconds"] / total_s, 4),
                 "GB/s": round(d["bytes"] / d["seconds"] / 1e9, 1),
                 "TFLOP/s": round(d["flops"] / d["seconds"] / 1e12, 2)} for d in kern]
+    # the FP32-pipe-bound kernels against the FP32 arithmetic peak: SMs x 128
+    # FP32 lanes x 2 flops per FMA x the SM clock sampled in the timed region
+    # (a measured register-only FFMA2 loop reaches 0.99 of this)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu = [{"kernel": d["name"], "bound": "alu", "achieved": d["flops"] / d["seconds"] / 1e12, "peak": fp32_peak,
+            "unit": "TFLOP/s", "frac": d["flops"] / d["seconds"] / 1e12 / fp32_peak,
+            "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (n_sm, sm_mhz)}
+           for d in kern if d["name"] in ("contract_fields_f32", "eo_hop_to_even_f16", "eo_hop_to_odd_Mp_f16")]
     dslash = [_dslash_roofline(g, abi, torch, peak, prec, nrhs)
               for prec in (abi.TSM_F16, abi.TSM_F32) for nrhs in (1, 12)]
 
@@ -975,6 +985,7 @@ def main():
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline,
             "kernels": kernels[:8],
+            "alu_roofline": alu,
             "dslash": dslash,
             "iterations": {"lp_mean": round(lp_iters, 1), "hp_mean": round(hp_iters, 1)},
             "e2e": e2e,
