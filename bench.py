@@ -413,9 +413,10 @@ def measured_traffic(kernel_class):
 
 def probe(args):
     """Small, self-contained workloads for profiler captures (no timing output).
-    The correction solves run on the calling thread (TSM_STREAMS=1): a
-    profiler serialises the kernels anyway, and the worker thread's graph
-    captures beside the main thread's do not run under ncu."""
+    `--probe tsm` runs a first TSM step (workspaces, autotuner, graphs) and a
+    steady-state one inside the NVTX range "tsm_step".  The correction solves
+    run on the calling thread (TSM_STREAMS=1): a profiler serialises the
+    kernels anyway, and one stream keeps the launch order readable."""
     import ctypes
 
     os.environ.setdefault("TSM_STREAMS", "1")
@@ -441,8 +442,16 @@ def probe(args):
     else:
         flag = abi.TSM_SOLVER_EO if args.precond == "eo" else 0
         lp = (abi.TSM_SOLVER_LP_F16 if args.lp == "f16" else abi.TSM_SOLVER_LP_BF16) | flag
-        g.tsm(WORKLOAD["kappa"], WORKLOAD["mu"], args.nrhs, args.n_hp, WORKLOAD["rho_lp"], WORKLOAD["rho_hp"], lp,
-              abi.TSM_SOLVER_F32_RELIABLE | flag, 11, api.momentum_table(9), nrhs_per_launch=args.nrhs)
+
+        def step(seed):
+            g.tsm(WORKLOAD["kappa"], WORKLOAD["mu"], args.nrhs, args.n_hp, WORKLOAD["rho_lp"], WORKLOAD["rho_hp"], lp,
+                  abi.TSM_SOLVER_F32_RELIABLE | flag, seed, api.momentum_table(9), nrhs_per_launch=args.nrhs)
+        step(10)  # first step: workspaces, autotuner timings, graph captures
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("tsm_step")  # a steady-state step (ncu --nvtx --nvtx-include tsm_step/)
+        step(11)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     g.close()
     ctx.close()
