@@ -282,8 +282,9 @@ int tsm_loops_backward(tsm_gauge* g, double kappa, double mu, int prec,
  * summed (not averaged) over the sources.  t0_host (optional, nsrc values)
  * gives each source's timeslice, or -1 for a volume source; only the
  * timeslices a source touches are contracted (t0, and t0 - 1 for the time
- * derivative).  The momentum list must hold -p with every p.  accumulate != 0
- * adds to out_dev.  Asynchronous on `stream`. */
+ * derivative).  Both flavour combinations are formed per site before the
+ * Fourier sums.  accumulate != 0 adds to out_dev.  Asynchronous on
+ * `stream`. */
 int tsm_contract_tdil(tsm_gauge* g, int prec, const void* s_dev,
                       const void* eta_dev, int nsrc, const int* t0_host,
                       int n_mom, const int* mom, double* out_dev,

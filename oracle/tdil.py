@@ -41,11 +41,17 @@ def _bilinear(a, g, b):
     return np.einsum("...sc,sr,...rc->...", np.conj(a), g, b)
 
 
-def standard_densities(u, eta, s):
+def standard_densities(u, eta, s, only=None):
     """Per-site densities of the 160 insertions from one source eta and its
-    solution s = M(mu)^{-1} eta: complex128 (160, t, z, y, x)."""
+    solution s = M(mu)^{-1} eta: complex128 (160, t, z, y, x).  ``only`` (a
+    collection of insertion indices) evaluates the same formulas for those
+    insertions (both flavour combinations of each listed Gamma and direction)
+    and leaves the others zero."""
     out = np.zeros((N_INSERTIONS,) + eta.shape[:-2], dtype=np.complex128)
+    want = (lambda i: True) if only is None else (lambda i: (i % 80) in {k % 80 for k in only})
     for g in range(16):
+        if not want(g):
+            continue
         gm = INSERTIONS[g]
         gd = GAMMA5 @ gm.conj().T @ GAMMA5
         du = _bilinear(eta, gm, s)
@@ -58,6 +64,8 @@ def standard_densities(u, eta, s):
         ef, eb = lattice.fwd(eta, m), lattice.bwd(eta, m)
         sf, sb = lattice.fwd(s, m), lattice.bwd(s, m)
         for g in range(16):
+            if not want(16 + 16 * m + g):
+                continue
             gm = INSERTIONS[g]
             gd = GAMMA5 @ gm.conj().T @ GAMMA5
             # u: psibar(y) K psi(z) -> eta(y)^dag K s(z)

@@ -98,6 +98,47 @@ __device__ __forceinline__ void store_traces(cplx<R>* out, size_t V, const cplx<
   ((out[(size_t)G * V] = insertion_trace<G>(m, scale)), ...);
 }
 
+// The standard estimator's two traces of a 4x4 matrix m (no g5 row factor):
+//   u:  sum_a Gamma_g[a][b] m[a][b]
+//   d:  sum_a g5_a g5_b conj(Gamma_g[a][b]) m[b][a]   (b = col_a),
+// the second being the trace with g5 Gamma_g^dag g5 that the d flavour
+// needs (its projection is taken at -p and conjugated afterwards).
+template <int G, typename R>
+__device__ __forceinline__ void std_traces(cplx<R>& tu, cplx<R>& td, const cplx<R> (&m)[16], R scale) {
+  constexpr Mono4 q = gamma_ins(G);
+  tu = mk<R>(0, 0);
+  td = mk<R>(0, 0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int b = q.col[a], ph = q.ph[a];
+    const cplx<R> x = m[4 * a + b], y = m[4 * b + a];
+    // u: i^ph x;  d: sg conj(i^ph) y = sg i^(-ph) y
+    const cplx<R> ux = ph == 0 ? x : (ph == 1 ? mk<R>(-x.im, x.re) : (ph == 2 ? mk<R>(-x.re, -x.im) : mk<R>(x.im, -x.re)));
+    const cplx<R> dy = ph == 0 ? y : (ph == 1 ? mk<R>(y.im, -y.re) : (ph == 2 ? mk<R>(-y.re, -y.im) : mk<R>(-y.im, y.re)));
+    const R sg = ((a < 2) == (b < 2)) ? scale : -scale;
+    tu = tu + scale * ux;
+    td = td + sg * dy;
+  }
+}
+// The two flavour combinations per site: d = sd conj(t_d) (sd = +1 for the
+// ultra-local pass, -1 for the derivative ones: the d form of the
+// derivative's two terms comes with the opposite sign), out[g] = u - d
+// (with tau_3), out[16 + g] = u + d.  The conjugate is taken per site, so
+// that no sum over sites ever carries the nearly equal real parts of u and d.
+template <int G, typename R>
+__device__ __forceinline__ void store_std_combos(cplx<R>* out, size_t V, const cplx<R> (&m)[16], R scale, R sd) {
+  cplx<R> tu, td;
+  std_traces<G>(tu, td, m, scale);
+  const cplx<R> d = mk<R>(sd * td.re, -sd * td.im);
+  out[(size_t)G * V] = tu - d;
+  out[(size_t)(16 + G) * V] = tu + d;
+}
+template <typename R, int... G>
+__device__ __forceinline__ void store_std_traces(cplx<R>* out, size_t V, const cplx<R> (&m)[16], R scale, R sd,
+                                                 std::integer_sequence<int, G...>) {
+  (store_std_combos<G>(out, V, m, scale, sd), ...);
+}
+
 namespace {
 
 struct HostCplx {
@@ -538,18 +579,18 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
   }
 }
 
-// z transform (FP64), the derivative shift and the Gamma insertions.  Block
-// (t, group): group = 2 pass + k holds one 4x4 matrix field (16 fields).
+// z transform (FP64), the derivative shift and the loop prefactor.  Block
+// (t, group): group = 2 pass + k holds 16 fields of one pass; each thread
+// owns (momentum, field) pairs and writes its loop values directly.
 __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restrict__ part, const int* __restrict__ mom,
                                                          int n_mom, Geom g, int rad, double mup, double* out,
-                                                         int accumulate) {
+                                                         int accumulate, int unit_prefactor = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lz = g.L[2], lt = g.L[3];
   const int t = blockIdx.x, group = blockIdx.y;
   const int pass = group >> 1, k = group & 1;
   const int nx = 2 * rad + 1, nxy = nx * nx;
-  double2* zs = reinterpret_cast<double2*>(smem_raw);  // [n_mom][16]
-  double2* twz = zs + (size_t)n_mom * 16;               // [nx][lz]
+  double2* twz = reinterpret_cast<double2*>(smem_raw);  // [nx][lz]
   for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
     const int n = q / lz - rad, zz = q % lz;
     double sn, cs;
@@ -559,6 +600,10 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
   __syncthreads();
   const int field0 = pass * NF + k * 16;
   const int tm1 = (t + lt - 1) % lt;
+  // prefactor: k = 0 -> -2 i mu', k = 1 -> 2 (the fields are the insertion traces already);
+  // 1 for both when the fields carry their flavour factors (standard estimator)
+  const double pre = unit_prefactor ? 1.0 : ((k == 0) ? 0.0 : 2.0);
+  const double pim = (unit_prefactor || k != 0) ? 0.0 : -2.0 * mup;
   for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
     const int m = q / 16, e = q % 16;
     const int mx = mom[3 * m], my = mom[3 * m + 1], mz = mom[3 * m + 2];
@@ -585,16 +630,8 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
       re = r2;
       im = i2;
     }
-    zs[q] = make_double2(re, im);
-  }
-  __syncthreads();
-  // prefactor: k = 0 -> -2 i mu', k = 1 -> 2 (the fields are the insertion traces already)
-  const double pre = (k == 0) ? 0.0 : 2.0, pim = (k == 0) ? -2.0 * mup : 0.0;
-  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
-    const int m = q / 16, gi = q % 16;
-    const double re = zs[m * 16 + gi].x, im = zs[m * 16 + gi].y;
     const double lr = pre * re - pim * im, li = pre * im + pim * re;
-    const int ins = 80 * k + (pass == 0 ? gi : 16 + 16 * (pass - 1) + gi);
+    const int ins = 80 * k + (pass == 0 ? e : 16 + 16 * (pass - 1) + e);
     double* o = out + (((size_t)ins * n_mom + m) * lt + t) * 2;
     if (accumulate) {
       o[0] += lr;
@@ -611,12 +648,14 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
 // time dilution) and their solutions s = M(mu)^{-1} eta, the bilinear
 // psibar(y) K psi(z) is estimated by eta(y)^dag K s(z) for the u flavour and,
 // through g5-hermiticity, by conj(eta(z)^dag g5 K^dag g5 s(y)) for the d
-// flavour.  Both need, per site, only the open 4x4 matrices (no g5 factor)
+// flavour.  Both come from the 4x4 matrices (no g5 factor)
 //   M[a][b]     = sum_c conj(eta_ac(x)) s_bc(x)
 //   D_mu[a][b]  = 1/4 sum_c [conj(eta_ac(x)) (U_mu(x) s(x+mu))_bc - conj(eta_ac(x+mu)) (U_mu(x)^dag s(x))_bc]
 // (the derivative's backward terms are D_mu at x - mu, applied after the
-// projection as in the one-end route).  A source on timeslice t0 touches
-// M and the F part of D on t0 and the G part of D_t on t0 - 1 only.
+// projection as in the one-end route), traced per site with Gamma_g (u) and
+// with g5 Gamma_g^dag g5 (d) before any sum over sites, for the FP32
+// accuracy reason given at the top of this file.  A source on timeslice t0
+// touches M and the F part of D on t0 and the G part of D_t on t0 - 1 only.
 template <typename R>
 struct TdilArgs {
   Geom g;
@@ -625,7 +664,7 @@ struct TdilArgs {
   const void* links;
   const int* t0;  // per source: its timeslice, or -1 for a volume source
   int nsrc;
-  cplx<R>* F;     // [80][V]: pass * 16 + 4 a + b
+  cplx<R>* F;     // [160][V]: pass * 32 + (0: u - d, 16: u + d) + g
 };
 
 template <typename R>
@@ -688,105 +727,10 @@ __global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) tdil_fields_ke
     }
   }
   const R scale = pass ? (R)0.25 : (R)1;
-  cplx<R>* out = a.F + (size_t)pass * 16 * V + i;
-#pragma unroll
-  for (int k = 0; k < 16; ++k) out[(size_t)k * V] = scale * m[k];
+  cplx<R>* out = a.F + (size_t)pass * 32 * V + i;
+  store_std_traces(out, V, m, scale, pass ? (R)-1 : (R)1, std::make_integer_sequence<int, 16>{});
 }
 
-// z transform, derivative shift and both flavours.  Block (t, group): group
-// 0 is M, group 1 + mu is D_mu.  u(p) = Gamma . Mt(p);  d(p) = +-conj(G' . Mt(-p))
-// with G' = g5 Gamma^dag g5 (+ for M, - for D); the derivative's shift is
-// the factor 1 + e^{-i p_mu} (spatial mu, applied to u and d at p) or the
-// sum of timeslices t and t - 1 (mu = t).  Outputs u - d (with tau_3) and
-// u + d (without).
-__global__ void __launch_bounds__(Z_BS) tdil_z_kernel(const double2* __restrict__ part, const int* __restrict__ mom,
-                                                      const int* __restrict__ mneg, int n_mom, Geom g, int rad,
-                                                      double* out, int accumulate) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lz = g.L[2], lt = g.L[3];
-  const int t = blockIdx.x, group = blockIdx.y;
-  const int nx = 2 * rad + 1, nxy = nx * nx;
-  double2* zs = reinterpret_cast<double2*>(smem_raw);  // [n_mom][16]
-  double2* twz = zs + (size_t)n_mom * 16;               // [nx][lz]
-  for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
-    const int n = q / lz - rad, zz = q % lz;
-    double sn, cs;
-    sincospi(2.0 * (double)(((n * zz) % lz + lz) % lz) / (double)lz, &sn, &cs);
-    twz[q] = make_double2(cs, -sn);
-  }
-  __syncthreads();
-  const int field0 = group * 16;
-  const int tm1 = (t + lt - 1) % lt;
-  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
-    const int m = q / 16, e = q % 16;
-    const int mx = mom[3 * m], my = mom[3 * m + 1], mz = mom[3 * m + 2];
-    const int nn = (mx + rad) * nx + (my + rad);
-    double re = 0.0, im = 0.0;
-    for (int zz = 0; zz < lz; ++zz) {
-      double2 p = part[((size_t)(zz + lz * t) * nxy + nn) * 80 + field0 + e];
-      if (group == 4) {
-        const double2 p1 = part[((size_t)(zz + lz * tm1) * nxy + nn) * 80 + field0 + e];
-        p.x += p1.x;
-        p.y += p1.y;
-      }
-      const double2 w = twz[(mz + rad) * lz + zz];
-      re += p.x * w.x - p.y * w.y;
-      im += p.x * w.y + p.y * w.x;
-    }
-    zs[q] = make_double2(re, im);
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
-    const int m = q / 16, gi = q % 16;
-    const int mb = mneg[m];
-    double ur = 0.0, ui = 0.0, dr = 0.0, di = 0.0;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int b = c_gamma.col[gi][a];
-      const double vr = c_gamma.re[gi][a], vi = c_gamma.im[gi][a];
-      const double2 x = zs[m * 16 + 4 * a + b];
-      ur += vr * x.x - vi * x.y;
-      ui += vr * x.y + vi * x.x;
-      // g5 Gamma^dag g5 has conj(v) at (b, a), times g5_b g5_a
-      const double sg = ((a < 2) == (b < 2)) ? 1.0 : -1.0;
-      const double2 y = zs[mb * 16 + 4 * b + a];
-      dr += sg * (vr * y.x + vi * y.y);
-      di += sg * (vr * y.y - vi * y.x);
-    }
-    // d = +-conj(.)
-    const double sd = group == 0 ? 1.0 : -1.0;
-    dr = sd * dr;
-    di = -sd * di;
-    if (group >= 1 && group <= 3) {  // O(p) = (1 + e^{-2 pi i n_mu / L_mu}) D(p)
-      const int nmu = group == 1 ? mom[3 * m] : (group == 2 ? mom[3 * m + 1] : mom[3 * m + 2]);
-      const int L = g.L[group - 1];
-      double sn, cs;
-      sincospi(2.0 * (double)(((nmu % L) + L) % L) / (double)L, &sn, &cs);
-      const double fr = 1.0 + cs, fi = -sn;
-      double r2 = ur * fr - ui * fi, i2 = ur * fi + ui * fr;
-      ur = r2;
-      ui = i2;
-      r2 = dr * fr - di * fi;
-      i2 = dr * fi + di * fr;
-      dr = r2;
-      di = i2;
-    }
-    const int ins = group == 0 ? gi : 16 + 16 * (group - 1) + gi;
-    double* o0 = out + (((size_t)ins * n_mom + m) * lt + t) * 2;         // with tau_3: u - d
-    double* o1 = out + (((size_t)(80 + ins) * n_mom + m) * lt + t) * 2;  // without: u + d
-    if (accumulate) {
-      o0[0] += ur - dr;
-      o0[1] += ui - di;
-      o1[0] += ur + dr;
-      o1[1] += ui + di;
-    } else {
-      o0[0] = ur - dr;
-      o0[1] = ui - di;
-      o1[0] = ur + dr;
-      o1[1] = ui + di;
-    }
-  }
-}
 
 // Hopping parameter expansion of the ultra-local insertions: their loops
 // come from the remainder field Y^4 s (A), plus the exact part of the first
@@ -1059,7 +1003,7 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
     TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, w.v.p, nsrc, rad, w.fields.p,
                                                          w.part.as<double2>(), st, prof ? &ev_f : nullptr,
                                                          prof ? &ev_xy : nullptr)));
-  const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
+  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
   TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   if (prof) TSM_TRY(ev_z.begin(st));
   count_launches(1);
@@ -1105,13 +1049,13 @@ int contract_ws_slot(tsm_gauge* g, int slot, ContractWorkspace** out, cudaStream
 }
 
 int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, const void* eta_dev, int nsrc,
-              const std::vector<int>& t0, int rad, const std::vector<int>& mneg, int n_mom, const int* mom_host,
+              const std::vector<int>& t0, int rad, int n_mom, const int* mom_host,
               double* out_dev, int accumulate, cudaStream_t st);
 
 // argument checks shared by the standard-estimator entries: per-source
-// timeslices, momentum radius and the index of -p for every p
+// timeslices and the momentum radius
 int tdil_setup(const tsm_gauge* g, int prec, int nsrc, const int* t0_host, int n_mom, const int* mom_host,
-               std::vector<int>& t0, int& rad, std::vector<int>& mneg) {
+               std::vector<int>& t0, int& rad) {
   if (prec != TSM_F32 && prec != TSM_F64)
     return fail(TSM_ERR_INVALID_ARG, "contraction takes F32 or F64 fields, got precision %d", prec);
   if (!has_prec(g, prec)) return fail(TSM_ERR_INVALID_ARG, "gauge has no copy in precision %d", prec);
@@ -1123,20 +1067,12 @@ int tdil_setup(const tsm_gauge* g, int prec, int nsrc, const int* t0_host, int n
       t0[r] = t0_host[r];
     }
   rad = 0;
-  mneg.assign(n_mom, -1);
-  for (int m = 0; m < n_mom; ++m) {
+  for (int m = 0; m < n_mom; ++m)
     for (int d = 0; d < 3; ++d) {
       const int n = mom_host[3 * m + d];
       if (n > 8 || n < -8) return fail(TSM_ERR_INVALID_ARG, "momentum component %d outside [-8, 8]", n);
       rad = std::max(rad, n < 0 ? -n : n);
     }
-    mneg[m] = -1;
-    for (int k = 0; k < n_mom; ++k)
-      if (mom_host[3 * k] == -mom_host[3 * m] && mom_host[3 * k + 1] == -mom_host[3 * m + 1] &&
-          mom_host[3 * k + 2] == -mom_host[3 * m + 2])
-        mneg[m] = k;
-    if (mneg[m] < 0) return fail(TSM_ERR_INVALID_ARG, "the momentum list must hold -p with every p");
-  }
   return TSM_OK;
 }
 
@@ -1144,35 +1080,33 @@ int tdil_setup(const tsm_gauge* g, int prec, int nsrc, const int* t0_host, int n
 
 int contract_tdil(tsm_gauge* g, int prec, const void* s_dev, const void* eta_dev, int nsrc, const int* t0_host,
                   int n_mom, const int* mom_host, double* out_dev, int accumulate, cudaStream_t st) {
-  std::vector<int> t0, mneg;
+  std::vector<int> t0;
   int rad = 0;
-  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad, mneg));
+  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad));
   ContractWorkspace* wp;
   TSM_TRY(contract_ws_slot(g, 0, &wp, st));
   std::lock_guard<std::mutex> wlock(wp->mu);
   TSM_TRY(wp->order.enter(st));
-  TSM_TRY(tdil_body(g, *wp, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, out_dev, accumulate, st));
+  TSM_TRY(tdil_body(g, *wp, prec, s_dev, eta_dev, nsrc, t0, rad, n_mom, mom_host, out_dev, accumulate, st));
   return wp->order.leave(st);
 }
 
 namespace {
 
 int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, const void* eta_dev, int nsrc,
-              const std::vector<int>& t0, int rad, const std::vector<int>& mneg, int n_mom, const int* mom_host,
+              const std::vector<int>& t0, int rad, int n_mom, const int* mom_host,
               double* out_dev, int accumulate, cudaStream_t st) {
   const int V = g->geom.V;
   const int lt = g->geom.L[3];
   const int nx = 2 * rad + 1;
   const int lz = g->geom.L[2];
   const size_t cs = prec == TSM_F32 ? sizeof(cplx<float>) : sizeof(cplx<double>);
-  TSM_TRY(w.fields.reserve((size_t)80 * V * cs));
-  TSM_TRY(w.part.reserve((size_t)lz * lt * 80 * nx * nx * sizeof(double2)));
+  TSM_TRY(w.fields.reserve((size_t)160 * V * cs));
+  TSM_TRY(w.part.reserve((size_t)lz * lt * 160 * nx * nx * sizeof(double2)));
   TSM_TRY(w.mom.reserve(sizeof(int) * 3 * (size_t)n_mom));
-  TSM_TRY(w.aux.reserve(sizeof(int) * ((size_t)n_mom + nsrc)));
-  int* mneg_dev = w.aux.as<int>();
-  int* t0_dev = mneg_dev + n_mom;
+  TSM_TRY(w.aux.reserve(sizeof(int) * (size_t)nsrc));
+  int* t0_dev = w.aux.as<int>();
   TSM_CUDA(cudaMemcpyAsync(w.mom.p, mom_host, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, st));
-  TSM_CUDA(cudaMemcpyAsync(mneg_dev, mneg.data(), sizeof(int) * n_mom, cudaMemcpyHostToDevice, st));
   TSM_CUDA(cudaMemcpyAsync(t0_dev, t0.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
   const unsigned nblk = (unsigned)((V + FLD_BS - 1) / FLD_BS);
   count_launches(1);
@@ -1180,18 +1114,19 @@ int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, c
     TdilArgs<float> a{g->geom, s_dev, eta_dev, g->links[TSM_F32].p, t0_dev, nsrc, w.fields.as<cplx<float>>()};
     tdil_fields_kernel<float, TSM_F32, TSM_F32><<<nblk * 5, FLD_BS, 0, st>>>(a);
     TSM_CUDA(cudaGetLastError());
-    TSM_TRY(launch_xy<float>(g, rad, w.fields.p, 80, w.part.as<double2>(), st));
+    TSM_TRY(launch_xy<float>(g, rad, w.fields.p, 160, w.part.as<double2>(), st));
   } else {
     TdilArgs<double> a{g->geom, s_dev, eta_dev, g->links[TSM_F64].p, t0_dev, nsrc, w.fields.as<cplx<double>>()};
     tdil_fields_kernel<double, TSM_F64, TSM_F64><<<nblk * 5, FLD_BS, 0, st>>>(a);
     TSM_CUDA(cudaGetLastError());
-    TSM_TRY(launch_xy<double>(g, rad, w.fields.p, 80, w.part.as<double2>(), st));
+    TSM_TRY(launch_xy<double>(g, rad, w.fields.p, 160, w.part.as<double2>(), st));
   }
-  const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
-  TSM_CUDA(cudaFuncSetAttribute(tdil_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
+  // the fields carry their flavour factors already: unit prefactors
+  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
+  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   count_launches(1);
-  tdil_z_kernel<<<dim3(lt, 5), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), mneg_dev, n_mom, g->geom,
-                                                   rad, out_dev, accumulate);
+  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), n_mom, g->geom, rad, 0.0,
+                                                       out_dev, accumulate, 1);
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }
@@ -1203,9 +1138,9 @@ int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_
                  cudaStream_t st) {
   for (int d = 0; d < 4; ++d)
     if (g->geom.L[d] < 4) return fail(TSM_ERR_INVALID_ARG, "the expansion's exact part needs every extent >= 4");
-  std::vector<int> t0, mneg;
+  std::vector<int> t0;
   int rad = 0;
-  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad, mneg));
+  TSM_TRY(tdil_setup(g, prec, nsrc, t0_host, n_mom, mom_host, t0, rad));
   const int lt = g->geom.L[3];
   int m0 = -1;
   for (int m = 0; m < n_mom; ++m)
@@ -1242,8 +1177,8 @@ int contract_hpe(tsm_gauge* g, double kappa, double mu, int prec, const void* s_
   TSM_TRY(hop_general(g, prec, ya, nullptr, yb, nsrc, 0.0, 0.0, h0, h1, st));
   TSM_TRY(hop_general(g, prec, yb, nullptr, ya, nsrc, 0.0, 0.0, h0, h1, st));
   TSM_TRY(hop_general(g, prec, ya, nullptr, yb, nsrc, 0.0, 0.0, h0, h1, st));
-  TSM_TRY(tdil_body(g, w, prec, yb, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, tmp_a, 0, st));
-  TSM_TRY(tdil_body(g, w, prec, s_dev, eta_dev, nsrc, t0, rad, mneg, n_mom, mom_host, tmp_b, 0, st));
+  TSM_TRY(tdil_body(g, w, prec, yb, eta_dev, nsrc, t0, rad, n_mom, mom_host, tmp_a, 0, st));
+  TSM_TRY(tdil_body(g, w, prec, s_dev, eta_dev, nsrc, t0, rad, n_mom, mom_host, tmp_b, 0, st));
   std::vector<double2> exh(160);
   for (int i = 0; i < 160; ++i) exh[i] = make_double2(ex[i].re, ex[i].im);
   TSM_CUDA(cudaMemcpyAsync(ex_dev, exh.data(), sizeof(double2) * 160, cudaMemcpyHostToDevice, st));
@@ -1336,7 +1271,7 @@ int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, cons
   else
     TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, v_dev, nsrc, rad, f_dev, part, st, nullptr,
                                                          nullptr)));
-  const size_t zsmem = (size_t)n_mom * 16 * sizeof(double2) + (size_t)nx * lz * sizeof(double2);
+  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
   TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   count_launches(1);
   project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(part, mom_dev, n_mom, g->geom, rad, 2.0 * kappa * mu, out_dev,

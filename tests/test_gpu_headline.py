@@ -61,3 +61,31 @@ def test_headline_hp_solve_and_contraction(headline):
     for k, ins in enumerate(sel):
         err = np.linalg.norm(got[ins] - want[k]) / np.linalg.norm(want[k])
         assert err < 1e-6, (ins, err)
+
+
+@pytest.mark.parametrize("t0", [5, -1])
+def test_headline_standard_estimator_contraction(headline, t0):
+    """The standard-estimator contraction (time dilution: the source kept on
+    timeslice 5; and a volume source) of an HP solution in FP32 against the
+    oracle's FP64 densities and direct Fourier sums, the same six insertions,
+    all 123 momenta: 1e-6."""
+    from oracle import tdil
+    g, u = headline
+    moms = momenta.momentum_list(9)
+    if t0 >= 0:
+        eta_nat = g.diluted_sources(SEED, 40, t0, 1, abi.TSM_F64)
+    else:
+        eta_nat = g.sources(SEED, 40, 1, abi.TSM_F64)
+    sol, st = g.invert(abi.TSM_OP_M, KAPPA, MU, abi.TSM_SOLVER_F32_RELIABLE | EO, 1e-9, eta_nat, 1)
+    s32 = g.pack(g.unpack(sol, abi.TSM_F64, 1), abi.TSM_F32)
+    e32 = g.pack(g.unpack(eta_nat, abi.TSM_F64, 1), abi.TSM_F32)
+    got = api.loops_complex(g.contract_tdil(abi.TSM_F32, s32, e32, 1, [t0], moms))
+    xs = g.unpack(s32, abi.TSM_F32, 1).cpu().numpy()[0]
+    eta = g.unpack(eta_nat, abi.TSM_F64, 1).cpu().numpy()[0]
+    sel = [0, 15, 80, 95,
+           contract.insertion_index(0, True, 0, 1), contract.insertion_index(1, True, 3, 8)]
+    dens = tdil.standard_densities(u, eta, xs, only=set(sel))
+    want = contract.project(dens[sel], DIMS, moms)
+    for k, ins in enumerate(sel):
+        err = np.linalg.norm(got[ins] - want[k]) / np.linalg.norm(want[k])
+        assert err < 1e-6, (t0, ins, err)

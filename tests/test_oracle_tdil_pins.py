@@ -57,3 +57,23 @@ def test_d_flavour_route_is_not_the_u_route():
     assert np.max(np.abs(d[0:16])) > 1e-3
     # ultra-local densities vanish off the source's timeslice
     assert np.max(np.abs(np.delete(d[0:16], 1, axis=1))) == 0.0
+
+
+def test_standard_density_subset_equals_full():
+    """standard_densities(only=...) evaluates the same formulas for the listed
+    insertions (both flavour combinations) and leaves the rest zero."""
+    import numpy as np
+    from oracle import lattice, tdil
+    from paper_1401_6750_gb300 import synth
+    dims = (2, 2, 2, 4)
+    u = lattice.effective_links(synth.gauge_links(dims, 0.4, 71), -1)
+    eta = tdil.diluted_source(dims, 72, 0, 1)
+    s = synth.gaussian_spinor(dims, 73)
+    full = tdil.standard_densities(u, eta, s)
+    part = tdil.standard_densities(u, eta, s, only={15, 17, 152})
+    keep = {15, 95, 17, 97, 72, 152}
+    for i in range(160):
+        if i in keep:
+            assert np.array_equal(part[i], full[i])
+        else:
+            assert not np.any(part[i])
