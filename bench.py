@@ -993,7 +993,7 @@ def main():
                            args.nrhs * g.volume * (96 * 4 + 48 * 2) / 1e9),
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline,
-            "kernels": kernels[:8],
+            "kernels": kernels[:14],
             "alu_roofline": alu,
             "dslash": dslash,
             "iterations": {"lp_mean": round(lp_iters, 1), "hp_mean": round(hp_iters, 1)},

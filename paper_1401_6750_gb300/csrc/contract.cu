@@ -234,6 +234,10 @@ constexpr int FLD_BS = 128;  // site-field kernel block
 constexpr int XY_BS = 256;   // x/y transform block
 constexpr int XY_NC = 7;     // momenta per accumulator set
 constexpr int Z_BS = 256;
+// grid of project_z_kernel: (timeslice, 10 field groups, slices of Z_BS (momentum, field) pairs)
+inline dim3 z_grid(int lt, int n_mom) {
+  return dim3(lt, 10, (unsigned)std::min((n_mom * 16 + Z_BS - 1) / Z_BS, 65535));
+}
 
 // Site fields (summed over the sources) in F[(pass*NF + f) * V + i], site fastest.
 template <typename R>
@@ -489,6 +493,24 @@ __global__ void __launch_bounds__(FLD_BS, 3) contract_fields_pairs_kernel(FieldA
   store_traces(out + 16 * V, V, m1, scale, std::make_integer_sequence<int, 16>{});
 }
 
+// Partial sums of the x/y transform per field precision: the FP32 sums are
+// stored as they are (float2; the float-float z sum takes them exactly),
+// the FP64 ones as double2.
+template <typename R>
+struct PartOf {
+  using type = double2;
+};
+template <>
+struct PartOf<float> {
+  using type = float2;
+};
+
+// Twiddle tables of the x/y transform hold e^{-2 pi i m / L} in the field precision.
+template <typename R>
+struct TwOf {
+  using type = cplx<R>;
+};
+
 __device__ __forceinline__ void twiddle(cplx<float>& o, int m, int L) {
   float sn, cs;
   sincospif(2.0f * (float)m / (float)L, &sn, &cs);
@@ -500,23 +522,44 @@ __device__ __forceinline__ void twiddle(cplx<double>& o, int m, int L) {
   o = mk<double>(cs, -sn);
 }
 
-// x then y transform of the nfields site fields of one (z, t) plane:
+__device__ __forceinline__ void store_part(float2* p, cplx<float> v) { *p = make_float2(v.re, v.im); }
+__device__ __forceinline__ void store_part(double2* p, cplx<double> v) { *p = make_double2(v.re, v.im); }
+
+// x then y transform of the site fields on one (z, t) plane:
 //   part[plane][(n_x, n_y)][f] = sum_{x,y} F_f(x, y) e^{-2 pi i (n_x x / Lx + n_y y / Ly)}
-// in chunks of nfc fields (a divisor of nfields sized to shared memory).  x: one thread per (field, row) reads the row
-// once from global memory and keeps XY_NC momenta in flight; y: one thread
-// per (field, n_x) over the rows in shared memory; the chunk's results are
+// Block (plane, chunk of nfc fields).  The chunk's planes (Lx Ly contiguous
+// values per field) are first copied to shared memory with coalesced loads,
+// rows padded to Lx + 1 values so that the row-wise reads below spread over
+// the banks; x: one thread per (field, row) keeps XY_NC momenta in flight;
+// y: one thread per (field, n_x) over the rows; the chunk's results are
 // staged so that the stores run along f.
 template <typename R>
-__global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __restrict__ F, Geom g, int rad,
-                                                            int nfc, int nfields, double2* __restrict__ part) {
+__global__ void __launch_bounds__(XY_BS, 4) contract_xy_kernel(const cplx<R>* __restrict__ F, Geom g, int rad,
+                                                            int nfc, int nfields,
+                                                            typename PartOf<R>::type* __restrict__ part) {
+  using TW = typename TwOf<R>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lx = g.L[0], ly = g.L[1];
+  const int lx = g.L[0], ly = g.L[1], lxp = lx + 1;
   const int nx = 2 * rad + 1, nxy = nx * nx;
-  const int plane = blockIdx.x;  // z + Lz * t
-  cplx<R>* X = reinterpret_cast<cplx<R>*>(smem_raw);  // [nfc][ly][nx]
-  cplx<R>* Y = X + (size_t)nfc * ly * nx;            // [nxy][nfc]
-  cplx<R>* twx = Y + (size_t)nxy * nfc;              // [lx][nx]
-  cplx<R>* twy = twx + (size_t)lx * nx;                // [ly][nx]
+  const int nchunk = nfields / nfc;
+  const int plane = blockIdx.x / nchunk;  // z + Lz * t
+  const int f0 = (blockIdx.x % nchunk) * nfc;
+  cplx<R>* S = reinterpret_cast<cplx<R>*>(smem_raw);  // [nfc][ly][lx + 1]
+  cplx<R>* X = S + (size_t)nfc * ly * lxp;             // [nfc][ly][nx]
+  cplx<R>* Y = X + (size_t)nfc * ly * nx;              // [nxy][nfc]
+  const size_t tw_off = ((size_t)(Y + (size_t)nxy * nfc - S) * sizeof(cplx<R>) + 15) & ~(size_t)15;
+  TW* twx = reinterpret_cast<TW*>(smem_raw + tw_off);  // [lx][nx], 16-byte aligned
+  TW* twy = twx + (size_t)lx * nx;                     // [ly][nx]
+  const size_t V = (size_t)g.V;
+  const int pv = lx * ly;
+  const cplx<R>* Fp = F + (size_t)f0 * V + (size_t)plane * pv;
+  // plane index q -> padded row offset, split once per thread and reused for every field of the chunk
+  for (int q = threadIdx.x; q < pv; q += blockDim.x) {
+    const int row = q / lx;
+    cplx<R>* dst = S + row * lxp + (q - row * lx);
+    const cplx<R>* src = Fp + q;
+    for (int f = 0; f < nfc; ++f) dst[(size_t)f * ly * lxp] = src[(size_t)f * V];
+  }
   for (int k = threadIdx.x; k < nx * lx; k += blockDim.x) {
     const int x = k / nx, n = k % nx - rad;
     twiddle(twx[k], ((n * x) % lx + lx) % lx, lx);
@@ -525,77 +568,107 @@ __global__ void __launch_bounds__(XY_BS) contract_xy_kernel(const cplx<R>* __res
     const int y = k / nx, n = k % nx - rad;
     twiddle(twy[k], ((n * y) % ly + ly) % ly, ly);
   }
-  const size_t V = (size_t)g.V;
-  const cplx<R>* Fp = F + (size_t)plane * lx * ly;
-  for (int f0 = 0; f0 < nfields; f0 += nfc) {
-    __syncthreads();
-    for (int task = threadIdx.x; task < nfc * ly; task += blockDim.x) {
-      const int row = task % ly, f = task / ly;
-      const cplx<R>* src = Fp + (size_t)(f0 + f) * V + (size_t)row * lx;
-      cplx<R>* dst = X + ((size_t)f * ly + row) * nx;
-      for (int n0 = 0; n0 < nx; n0 += XY_NC) {
-        cplx<R> acc[XY_NC];
+  __syncthreads();
+  for (int task = threadIdx.x; task < nfc * ly; task += blockDim.x) {
+    const int row = task % ly, f = task / ly;
+    const cplx<R>* src = S + ((size_t)f * ly + row) * lxp;
+    cplx<R>* dst = X + ((size_t)f * ly + row) * nx;
+    for (int n0 = 0; n0 < nx; n0 += XY_NC) {
+      cplx<R> acc[XY_NC];
 #pragma unroll
-        for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+      for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
 #pragma unroll 6
-        for (int x = 0; x < lx; ++x) {
-          const cplx<R> v = src[x];
-          const cplx<R>* tw = twx + (size_t)x * nx + n0;
-#pragma unroll
-          for (int j = 0; j < XY_NC; ++j)
-            if (n0 + j < nx) cmac(acc[j], v, tw[j]);
-        }
+      for (int x = 0; x < lx; ++x) {
+        const cplx<R> v = src[x];
+        const TW* tw = twx + (size_t)x * nx + n0;
 #pragma unroll
         for (int j = 0; j < XY_NC; ++j)
-          if (n0 + j < nx) dst[n0 + j] = acc[j];
+          if (n0 + j < nx) cmac(acc[j], v, tw[j]);
       }
+#pragma unroll
+      for (int j = 0; j < XY_NC; ++j)
+        if (n0 + j < nx) dst[n0 + j] = acc[j];
     }
-    __syncthreads();
-    for (int task = threadIdx.x; task < nfc * nx; task += blockDim.x) {
-      const int f = task % nfc, n_x = task / nfc;
-      const cplx<R>* src = X + (size_t)f * ly * nx + n_x;
-      for (int n0 = 0; n0 < nx; n0 += XY_NC) {
-        cplx<R> acc[XY_NC];
+  }
+  __syncthreads();
+  for (int task = threadIdx.x; task < nfc * nx; task += blockDim.x) {
+    const int f = task % nfc, n_x = task / nfc;
+    const cplx<R>* src = X + (size_t)f * ly * nx + n_x;
+    for (int n0 = 0; n0 < nx; n0 += XY_NC) {
+      cplx<R> acc[XY_NC];
 #pragma unroll
-        for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
+      for (int j = 0; j < XY_NC; ++j) acc[j] = mk<R>(0, 0);
 #pragma unroll 6
-        for (int row = 0; row < ly; ++row) {
-          const cplx<R> v = src[(size_t)row * nx];
-          const cplx<R>* tw = twy + (size_t)row * nx + n0;
-#pragma unroll
-          for (int j = 0; j < XY_NC; ++j)
-            if (n0 + j < nx) cmac(acc[j], v, tw[j]);
-        }
+      for (int row = 0; row < ly; ++row) {
+        const cplx<R> v = src[(size_t)row * nx];
+        const TW* tw = twy + (size_t)row * nx + n0;
 #pragma unroll
         for (int j = 0; j < XY_NC; ++j)
-          if (n0 + j < nx) Y[((size_t)n_x * nx + n0 + j) * nfc + f] = acc[j];
+          if (n0 + j < nx) cmac(acc[j], v, tw[j]);
       }
+#pragma unroll
+      for (int j = 0; j < XY_NC; ++j)
+        if (n0 + j < nx) Y[((size_t)n_x * nx + n0 + j) * nfc + f] = acc[j];
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nxy * nfc; k += blockDim.x) {
-      const int f = k % nfc, nn = k / nfc;
-      part[((size_t)plane * nxy + nn) * nfields + f0 + f] = make_double2((double)Y[k].re, (double)Y[k].im);
-    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < nxy * nfc; k += blockDim.x) {
+    const int f = k % nfc, nn = k / nfc;
+    store_part(part + ((size_t)plane * nxy + nn) * nfields + f0 + f, Y[k]);
   }
 }
 
-// z transform (FP64), the derivative shift and the loop prefactor.  Block
-// (t, group): group = 2 pass + k holds 16 fields of one pass; each thread
-// owns (momentum, field) pairs and writes its loop values directly.
-__global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restrict__ part, const int* __restrict__ mom,
+// Arithmetic of the z sum per part type: FP64 for FP64 partial sums,
+// float-float (about 44 bits, on the FP32 pipes) for FP32 ones, which it
+// takes exactly.  GB300's FP64 pipe is 1/64 of FP32: in FP64 this sum kept
+// it 87% busy.
+template <typename PT>
+struct ZReal {
+  using type = double;
+};
+template <>
+struct ZReal<float2> {
+  using type = dsf;
+};
+template <typename Z>
+__device__ __forceinline__ cplx<Z> zload(const float2& p) {
+  return mk<Z>(Z(p.x), Z(p.y));
+}
+template <typename Z>
+__device__ __forceinline__ cplx<Z> zload(const double2& p) {
+  return mk<Z>(Z(p.x), Z(p.y));
+}
+__device__ __forceinline__ double zdouble(double v) { return v; }
+__device__ __forceinline__ double zdouble(dsf v) { return (double)v; }
+
+// z transform, the derivative shift and the loop prefactor.  Block (t,
+// group, slice): group = 2 pass + k holds 16 fields of one pass; slice z
+// takes the (momentum, field) pairs z * Z_BS .. z * Z_BS + Z_BS - 1, one per
+// thread, written directly.  The block's phases (z twiddles, and the shift
+// factors of its direction) are tabulated in shared memory first.
+template <typename PT>
+__global__ void __launch_bounds__(Z_BS) project_z_kernel(const PT* __restrict__ part, const int* __restrict__ mom,
                                                          int n_mom, Geom g, int rad, double mup, double* out,
-                                                         int accumulate, int unit_prefactor = 0) {
+                                                         int accumulate, int unit_prefactor) {
+  using Z = typename ZReal<PT>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lz = g.L[2], lt = g.L[3];
   const int t = blockIdx.x, group = blockIdx.y;
   const int pass = group >> 1, k = group & 1;
   const int nx = 2 * rad + 1, nxy = nx * nx;
-  double2* twz = reinterpret_cast<double2*>(smem_raw);  // [nx][lz]
-  for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
-    const int n = q / lz - rad, zz = q % lz;
+  cplx<Z>* twz = reinterpret_cast<cplx<Z>*>(smem_raw);  // [nx][lz]: e^{-2 pi i n z / Lz}
+  cplx<Z>* shf = twz + (size_t)nx * lz;                   // [nx]: 1 + e^{-2 pi i n / L_mu}, mu = pass - 1
+  for (int q = threadIdx.x; q < nx * lz + nx; q += blockDim.x) {
     double sn, cs;
-    sincospi(2.0 * (double)(((n * zz) % lz + lz) % lz) / (double)lz, &sn, &cs);
-    twz[q] = make_double2(cs, -sn);
+    if (q < nx * lz) {
+      const int n = q / lz - rad, zz = q % lz;
+      sincospi(2.0 * (double)(((n * zz) % lz + lz) % lz) / (double)lz, &sn, &cs);
+      twz[q] = mk<Z>(Z(cs), Z(-sn));
+    } else if (pass >= 1 && pass <= 3) {
+      const int n = q - nx * lz - rad, L = g.L[pass - 1];
+      sincospi(2.0 * (double)(((n % L) + L) % L) / (double)L, &sn, &cs);
+      shf[n + rad] = mk<Z>(Z(1.0 + cs), Z(-sn));
+    }
   }
   __syncthreads();
   const int field0 = pass * NF + k * 16;
@@ -604,32 +677,21 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
   // 1 for both when the fields carry their flavour factors (standard estimator)
   const double pre = unit_prefactor ? 1.0 : ((k == 0) ? 0.0 : 2.0);
   const double pim = (unit_prefactor || k != 0) ? 0.0 : -2.0 * mup;
-  for (int q = threadIdx.x; q < n_mom * 16; q += blockDim.x) {
+  for (int q = blockIdx.z * blockDim.x + threadIdx.x; q < n_mom * 16; q += gridDim.z * blockDim.x) {
     const int m = q / 16, e = q % 16;
     const int mx = mom[3 * m], my = mom[3 * m + 1], mz = mom[3 * m + 2];
     const int nn = (mx + rad) * nx + (my + rad);
-    double re = 0.0, im = 0.0;
+    const cplx<Z>* tw = twz + (size_t)(mz + rad) * lz;
+    cplx<Z> acc = mk<Z>(Z(0.0), Z(0.0));
     for (int zz = 0; zz < lz; ++zz) {
-      double2 p = part[((size_t)(zz + lz * t) * nxy + nn) * 160 + field0 + e];
-      if (pass == 4) {  // O_t(t) = D_t(t) + D_t(t - 1)
-        const double2 p1 = part[((size_t)(zz + lz * tm1) * nxy + nn) * 160 + field0 + e];
-        p.x += p1.x;
-        p.y += p1.y;
-      }
-      const double2 w = twz[(mz + rad) * lz + zz];
-      re += p.x * w.x - p.y * w.y;
-      im += p.x * w.y + p.y * w.x;
+      cplx<Z> p = zload<Z>(part[((size_t)(zz + lz * t) * nxy + nn) * 160 + field0 + e]);
+      if (pass == 4)  // O_t(t) = D_t(t) + D_t(t - 1)
+        p = p + zload<Z>(part[((size_t)(zz + lz * tm1) * nxy + nn) * 160 + field0 + e]);
+      acc = acc + cmul(p, tw[zz]);
     }
-    if (pass >= 1 && pass <= 3) {  // O_mu(p) = (1 + e^{-2 pi i n_mu / L_mu}) D_mu(p)
-      const int nmu = pass == 1 ? mx : (pass == 2 ? my : mz);
-      const int L = g.L[pass - 1];
-      double sn, cs;
-      sincospi(2.0 * (double)(((nmu % L) + L) % L) / (double)L, &sn, &cs);
-      const double fr = 1.0 + cs, fi = -sn;
-      const double r2 = re * fr - im * fi, i2 = re * fi + im * fr;
-      re = r2;
-      im = i2;
-    }
+    if (pass >= 1 && pass <= 3)  // O_mu(p) = (1 + e^{-2 pi i n_mu / L_mu}) D_mu(p)
+      acc = cmul(acc, shf[(pass == 1 ? mx : (pass == 2 ? my : mz)) + rad]);
+    const double re = zdouble(acc.re), im = zdouble(acc.im);
     const double lr = pre * re - pim * im, li = pre * im + pim * re;
     const int ins = 80 * k + (pass == 0 ? e : 16 + 16 * (pass - 1) + e);
     double* o = out + (((size_t)ins * n_mom + m) * lt + t) * 2;
@@ -641,6 +703,22 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const double2* __restri
       o[1] = li;
     }
   }
+}
+
+// z transform of the partial sums of field precision R (FP32: float2 parts)
+template <typename R>
+int launch_z(const tsm_gauge* g, const void* part, const int* mom_dev, int n_mom, int rad, double mup, double* out,
+             int accumulate, int unit_prefactor, cudaStream_t st) {
+  using PT = typename PartOf<R>::type;
+  using Z = typename ZReal<PT>::type;
+  const int lz = g->geom.L[2], lt = g->geom.L[3], nx = 2 * rad + 1;
+  const size_t zsmem = ((size_t)nx * lz + nx) * sizeof(cplx<Z>);
+  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
+  count_launches(1);
+  project_z_kernel<PT><<<z_grid(lt, n_mom), Z_BS, zsmem, st>>>(static_cast<const PT*>(part), mom_dev, n_mom, g->geom,
+                                                               rad, mup, out, accumulate, unit_prefactor);
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
 }
 
 // ---------------------------------------------------------------- standard estimator (time dilution)
@@ -866,21 +944,25 @@ void ContractWsDeleter::operator()(ContractWorkspace* w) const { delete w; }
 
 namespace {
 
+// staged planes, x results, y results, alignment, twiddle tables (cs bytes per complex value)
 size_t xy_smem(const Geom& g, int rad, int nfc, size_t cs) {
   const int nx = 2 * rad + 1;
-  return cs * ((size_t)nfc * g.L[1] * nx + (size_t)nx * nx * nfc + (size_t)nx * (g.L[0] + g.L[1]));
+  return cs * ((size_t)nfc * g.L[1] * (g.L[0] + 1) + (size_t)nfc * g.L[1] * nx + (size_t)nx * nx * nfc +
+               (size_t)nx * (g.L[0] + g.L[1])) + 16;
 }
 
-// Largest chunk of fields (dividing nfields) whose transform fits in 160 KB; 0 if none.
+// Fields per block of the x/y transform: the largest of 8, 4, 2 dividing
+// nfields whose shared memory stays within 64 KB (three or more blocks per
+// SM), else a single field within the 227 KB a block may hold; 0 if none.
 int xy_chunk(const Geom& g, int rad, size_t cs, int nfields) {
-  for (int nfc : {32, 16, 8, 4, 2, 1})
-    if (nfields % nfc == 0 && xy_smem(g, rad, nfc, cs) <= 160 * 1024) return nfc;
-  return 0;
+  for (int nfc : {8, 4, 2})
+    if (nfields % nfc == 0 && xy_smem(g, rad, nfc, cs) <= 64 * 1024) return nfc;
+  return xy_smem(g, rad, 1, cs) <= 227 * 1024 ? 1 : 0;
 }
 
 // x/y transform of nfields site fields of type cplx<R> into part
 template <typename R>
-int launch_xy(tsm_gauge* g, int rad, const void* F, int nfields, double2* part, cudaStream_t st) {
+int launch_xy(tsm_gauge* g, int rad, const void* F, int nfields, void* part, cudaStream_t st) {
   const int nfc = xy_chunk(g->geom, rad, sizeof(cplx<R>), nfields);
   if (nfc == 0)
     return fail(TSM_ERR_INVALID_ARG, "plane %dx%d too large for the contraction", g->geom.L[0], g->geom.L[1]);
@@ -888,15 +970,16 @@ int launch_xy(tsm_gauge* g, int rad, const void* F, int nfields, double2* part, 
   auto kern = contract_xy_kernel<R>;
   TSM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   count_launches(1);
-  kern<<<g->geom.L[2] * g->geom.L[3], XY_BS, smem, st>>>(static_cast<const cplx<R>*>(F), g->geom, rad, nfc,
-                                                          nfields, part);
+  const unsigned nblk = (unsigned)(g->geom.L[2] * g->geom.L[3]) * (unsigned)(nfields / nfc);
+  kern<<<nblk, XY_BS, smem, st>>>(static_cast<const cplx<R>*>(F), g->geom, rad, nfc, nfields,
+                                  static_cast<typename PartOf<R>::type*>(part));
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;
 }
 
 // Site fields then x/y transform; F holds 160 V fields of type cplx<R>.
 template <typename R, int PS, int PL>
-int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsrc, int rad, void* F, double2* part,
+int launch_fields_xy(tsm_gauge* g, const void* s_dev, const void* v_dev, int nsrc, int rad, void* F, void* part,
                      cudaStream_t st, EventPair* ev_f, EventPair* ev_xy) {
   FieldArgs<R> a;
   a.g = g->geom;
@@ -1003,17 +1086,15 @@ int contract_loops(tsm_gauge* g, double kappa, double mu, int prec, const void* 
     TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, w.v.p, nsrc, rad, w.fields.p,
                                                          w.part.as<double2>(), st, prof ? &ev_f : nullptr,
                                                          prof ? &ev_xy : nullptr)));
-  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
-  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   if (prof) TSM_TRY(ev_z.begin(st));
-  count_launches(1);
-  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), n_mom, g->geom, rad,
-                                                      2.0 * kappa * mu, out_dev, accumulate);
+  if (prec == TSM_F32)
+    TSM_TRY(launch_z<float>(g, w.part.p, w.mom.as<int>(), n_mom, rad, 2.0 * kappa * mu, out_dev, accumulate, 0, st));
+  else
+    TSM_TRY(launch_z<double>(g, w.part.p, w.mom.as<int>(), n_mom, rad, 2.0 * kappa * mu, out_dev, accumulate, 0, st));
   if (prof) TSM_TRY(ev_z.end(st));
-  TSM_CUDA(cudaGetLastError());
   if (prof) {
     const double v = (double)V, n = (double)nsrc, b = spinor_site_bytes(prec), l = link_site_bytes(prec);
-    const double part_bytes = (double)lz * lt * nx * nx * 160 * 16;
+    const double part_bytes = (double)lz * lt * nx * nx * 160 * (prec == TSM_F32 ? 8 : 16);
     const double field_bytes = 160.0 * v * (double)cs;
     const double out_bytes = 160.0 * n_mom * lt * 16 * (accumulate ? 2 : 1);
     const char* pn = prec == TSM_F32 ? "f32" : "f64";
@@ -1122,13 +1203,8 @@ int tdil_body(tsm_gauge* g, ContractWorkspace& w, int prec, const void* s_dev, c
     TSM_TRY(launch_xy<double>(g, rad, w.fields.p, 160, w.part.as<double2>(), st));
   }
   // the fields carry their flavour factors already: unit prefactors
-  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
-  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
-  count_launches(1);
-  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(w.part.as<double2>(), w.mom.as<int>(), n_mom, g->geom, rad, 0.0,
-                                                       out_dev, accumulate, 1);
-  TSM_CUDA(cudaGetLastError());
-  return TSM_OK;
+  if (prec == TSM_F32) return launch_z<float>(g, w.part.p, w.mom.as<int>(), n_mom, rad, 0.0, out_dev, accumulate, 1, st);
+  return launch_z<double>(g, w.part.p, w.mom.as<int>(), n_mom, rad, 0.0, out_dev, accumulate, 1, st);
 }
 
 }  // namespace
@@ -1271,13 +1347,8 @@ int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, cons
   else
     TSM_TRY((launch_fields_xy<double, TSM_F64, TSM_F64>(g, s_dev, v_dev, nsrc, rad, f_dev, part, st, nullptr,
                                                          nullptr)));
-  const size_t zsmem = (size_t)nx * lz * sizeof(double2);
-  TSM_CUDA(cudaFuncSetAttribute(project_z_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
-  count_launches(1);
-  project_z_kernel<<<dim3(lt, 10), Z_BS, zsmem, st>>>(part, mom_dev, n_mom, g->geom, rad, 2.0 * kappa * mu, out_dev,
-                                                      accumulate);
-  TSM_CUDA(cudaGetLastError());
-  return TSM_OK;
+  if (prec == TSM_F32) return launch_z<float>(g, part, mom_dev, n_mom, rad, 2.0 * kappa * mu, out_dev, accumulate, 0, st);
+  return launch_z<double>(g, part, mom_dev, n_mom, rad, 2.0 * kappa * mu, out_dev, accumulate, 0, st);
 }
 
 }  // namespace tsm
