@@ -4,9 +4,10 @@ on the GPU against the oracle's literal per-insertion densities.
 Both sides receive the same seeded synthetic "solutions" s (Gaussian spinors,
 rounded to the storage type for the FP32 path).  The oracle forms every
 insertion's density directly and projects with a direct Fourier sum; the GPU
-forms the open 4x4 Dirac matrices, projects them separably and applies Gamma
-afterwards.  Tolerance, normwise per insertion over (momentum, timeslice):
-FP64 1e-11; FP32 1e-6 (FP32 products and short x/y sums, FP64 z sums).
+forms the 16 insertion traces per site and projects them separably (x and y
+per plane, then z).  Tolerance, normwise per insertion over (momentum,
+timeslice): FP64 1e-11; FP32 1e-6 (FP32 products and short x/y sums,
+float-float z sums).
 """
 import numpy as np
 import pytest
@@ -47,6 +48,24 @@ def test_contraction_matches_oracle(ctx, dims, t_bc, prec):
     moms = momenta.momentum_list(9)
     nat = g.pack(to_device(s), prec)
     out = api.loops_complex(g.contract(kappa, mu, prec, nat, nsrc, moms))
+    want = _oracle_loops(u, s, kappa, mu, dims, moms)
+    _compare(out, want, 1e-11 if prec == abi.TSM_F64 else 1e-6)
+    g.close()
+
+
+@pytest.mark.parametrize("dims,prec", [((24, 20, 2, 2), abi.TSM_F32), ((24, 20, 2, 2), abi.TSM_F64),
+                                       ((40, 40, 2, 2), abi.TSM_F64)])
+def test_contraction_large_planes_radius_8(ctx, dims, prec):
+    """Planes large enough, with momentum components up to 8, that the x/y
+    transform takes 4, 2 or a single field per block instead of 8 (its
+    shared memory per block grows with the plane and the radius)."""
+    kappa, mu = 0.125, 0.01
+    g, links = gauge(ctx, dims, 0.3, 6, -1)
+    u = lattice.effective_links(links, -1)
+    s = round_to(synth.gaussian_spinor(dims, 42, nrhs=2), prec)
+    moms = [(0, 0, 0), (8, 0, 0), (0, -8, 1), (3, 5, -8), (-7, 2, 4), (1, 1, 1)]
+    nat = g.pack(to_device(s), prec)
+    out = api.loops_complex(g.contract(kappa, mu, prec, nat, 2, moms))
     want = _oracle_loops(u, s, kappa, mu, dims, moms)
     _compare(out, want, 1e-11 if prec == abi.TSM_F64 else 1e-6)
     g.close()
