@@ -64,19 +64,28 @@ __global__ void k_scatter_eo(void* full, const void* even, const void* odd, Geom
   SpinorIO<PO>::store(full, (size_t)g.V, rhs, i, v);
 }
 
-// out = (cr + i ci g5) in on one parity (V/2 sites)
+// full -> even and odd halves, and diag_even = (cr + i ci g5) eta_e on the
+// even sites, in one pass
 template <int P>
-__global__ void k_diag(void* out, const void* in, double cr, double ci, int vh) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_split_eo(const void* full, void* even, void* odd, void* diag_even, double cr, double ci, Geom g) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int rhs = blockIdx.y;
-  if (j >= vh) return;
+  if (i >= g.V) return;
+  int c[4];
+  site_coords(g, i, c);
   using R = ew_real<P>;
   cplx<R> v[12];
-  SpinorIO<P>::load(in, (size_t)vh, rhs, j, v);
+  SpinorIO<P>::load(full, (size_t)g.V, rhs, i, v);
+  const size_t vh = (size_t)g.V / 2;
+  if ((c[0] + c[1] + c[2] + c[3]) & 1) {
+    SpinorIO<P>::store(odd, vh, rhs, i >> 1, v);
+    return;
+  }
+  SpinorIO<P>::store(even, vh, rhs, i >> 1, v);
   const R a = (R)cr, b = (R)ci;
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = a * v[k] + (k < 6 ? b : -b) * times_i(v[k]);
-  SpinorIO<P>::store(out, (size_t)vh, rhs, j, v);
+  SpinorIO<P>::store(diag_even, vh, rhs, i >> 1, v);
 }
 
 }  // namespace
@@ -364,7 +373,8 @@ struct SolverEO {
     return TSM_OK;
   }
 
-  // eta (all sites, precise precision) in w.full
+  // eta split by parity (precise precision): eta_e, t1 = eta_o and
+  // tep = M_ee^{-1} eta_e (split_sources)
   static int solve(tsm_gauge* g, EoWorkspace& w, int nrhs, double kappa, double mu, double rho, int max_iter,
                    int out_prec, void* x_out, int gamma5_out, tsm_solve_stats* stats, cudaStream_t s) {
     const double mup = 2.0 * kappa * mu;
@@ -374,10 +384,7 @@ struct SolverEO {
     const size_t Vh = (size_t)V / 2;
     dim3 fg((V + EW_BS - 1) / EW_BS, nrhs), eg(((int)Vh + EW_BS - 1) / EW_BS, nrhs);
     set_shapes(w);
-    count_launches(7);
-    // split eta; t1 = eta_o, tep = M_ee^{-1} eta_e
-    k_gather_eo<T::PP><<<fg, EW_BS, 0, s>>>(w.full.p, w.eta_e.p, w.t1.p, g->geom);
-    k_diag<T::PP><<<eg, EW_BS, 0, s>>>(w.tep.p, w.eta_e.p, 1.0 / d, -mup / d, (int)Vh);
+    count_launches(4);
     {  // t1 = eta_o - M_oe M_ee^{-1} eta_e = eta_o + kappa H tep   (in place on t1)
       EpiStore<Rp, T::PP> e{w.t1.p, Vh, 0, RedSlots{nullptr, nullptr}};
       launch_dslash_eo<Rp, -1, T::PP, T::PLp>(w.nr_p, args(g, T::PLp, w.tep.p, w.t1.p, 1, kappa, 1.0, 0.0, kappa, 0.0, nrhs),
@@ -480,10 +487,16 @@ int solve_eo_kind(tsm_gauge* g, double kappa, double mu, double rho, int max_ite
   std::lock_guard<std::mutex> wlock(w.mu);
   TSM_TRY(w.order.enter(s));
   TSM_TRY(SolverEO<KIND>::reserve(g, w, nrhs, s));
+  // the source split by parity: eta_e, t1 = eta_o, tep = M_ee^{-1} eta_e
+  const double mup = 2.0 * kappa * mu, d = 1.0 + mup * mup;
   if (eta) {
     TSM_TRY(spinor_convert(g, T::PP, w.full.p, eta_prec, eta, nrhs, gamma5_io, s));
+    dim3 fg((g->geom.V + EW_BS - 1) / EW_BS, nrhs);
+    count_launches(1);
+    k_split_eo<T::PP><<<fg, EW_BS, 0, s>>>(w.full.p, w.eta_e.p, w.t1.p, w.tep.p, 1.0 / d, -mup / d, g->geom);
+    TSM_CUDA(cudaGetLastError());
   } else {
-    TSM_TRY(make_sources(g, seed, first, nrhs, T::PP, w.full.p, s));
+    TSM_TRY(make_sources_eo(g, seed, first, nrhs, T::PP, w.eta_e.p, w.t1.p, w.tep.p, 1.0 / d, -mup / d, s));
   }
   const int rc = SolverEO<KIND>::solve(g, w, nrhs, kappa, mu, rho, max_iter, out_prec, x_out, gamma5_io, stats, s);
   const int rc_order = w.order.leave(s);

@@ -121,6 +121,40 @@ __global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out, int t
   SpinorIO<P>::store(out, (size_t)V, r, i, v);
 }
 
+// The same Z4 sources split by parity for the even-odd solvers: site i of
+// field r goes to odd or even at i >> 1 (all extents even), and the even
+// sites also to diag_even as (cr + i ci g5) eta_e (M_ee^{-1} eta_e), in the
+// arithmetic of the element-wise kernels.
+template <int P>
+__global__ void z4_eo_kernel(uint64_t seed, uint64_t first, Geom g, void* even, void* odd, void* diag_even, double cr,
+                             double ci) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (i >= g.V) return;
+  uint64_t x[4] = {(uint64_t)i, 0ull, 0ull, 0ull};
+  philox4x64_10(x, seed, first + (uint64_t)r);
+  const uint64_t w = x[0];
+  using R = ew_real<P>;
+  cplx<R> v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int z = (int)((w >> (2 * k)) & 3ull);
+    v[k] = mk<R>((R)(z == 0 ? 1 : (z == 2 ? -1 : 0)), (R)(z == 1 ? 1 : (z == 3 ? -1 : 0)));
+  }
+  int c[4];
+  site_coords(g, i, c);
+  const size_t vh = (size_t)g.V / 2;
+  if ((c[0] + c[1] + c[2] + c[3]) & 1) {
+    SpinorIO<P>::store(odd, vh, r, i >> 1, v);
+    return;
+  }
+  SpinorIO<P>::store(even, vh, r, i >> 1, v);
+  const R a = (R)cr, b = (R)ci;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) v[k] = a * v[k] + (k < 6 ? b : -b) * times_i(v[k]);
+  SpinorIO<P>::store(diag_even, vh, r, i >> 1, v);
+}
+
 // ------------------------------------------------------------------ layout conversions
 template <int P>
 __global__ void pack_kernel(const double2* __restrict__ plain, void* native, int V, double scale) {
@@ -340,6 +374,21 @@ int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, in
     case TSM_BF16: z4_kernel<TSM_BF16><<<grid, BS, 0, s>>>(seed, first, V, out); break;
     case TSM_DS: z4_kernel<TSM_DS><<<grid, BS, 0, s>>>(seed, first, V, out); break;
     default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d", prec);
+  }
+  TSM_CUDA(cudaGetLastError());
+  return TSM_OK;
+}
+
+int make_sources_eo(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* even, void* odd,
+                    void* diag_even, double cr, double ci, cudaStream_t s) {
+  const int V = g->geom.V;
+  dim3 grid((V + BS - 1) / BS, nsrc);
+  count_launches(1);
+  switch (prec) {
+    case TSM_F64: z4_eo_kernel<TSM_F64><<<grid, BS, 0, s>>>(seed, first, g->geom, even, odd, diag_even, cr, ci); break;
+    case TSM_F32: z4_eo_kernel<TSM_F32><<<grid, BS, 0, s>>>(seed, first, g->geom, even, odd, diag_even, cr, ci); break;
+    case TSM_DS: z4_eo_kernel<TSM_DS><<<grid, BS, 0, s>>>(seed, first, g->geom, even, odd, diag_even, cr, ci); break;
+    default: return fail(TSM_ERR_INVALID_ARG, "bad precision %d for parity-split sources", prec);
   }
   TSM_CUDA(cudaGetLastError());
   return TSM_OK;

@@ -202,6 +202,10 @@ int dslash_apply_fixed(tsm_gauge* g, int prec, int op, double kappa, double mu, 
 
 // ---- fields (fields.cu)
 int make_sources(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* out, cudaStream_t s);
+// make_sources split by parity for the even-odd solvers (all extents even):
+// even and odd halves, and diag_even = (cr + i ci g5) applied to the even half
+int make_sources_eo(const tsm_gauge* g, uint64_t seed, uint64_t first, int nsrc, int prec, void* even, void* odd,
+                    void* diag_even, double cr, double ci, cudaStream_t s);
 // n_t fields: the source `source_id` kept on timeslices t_first .. t_first + n_t - 1, one each
 int make_diluted_sources(const tsm_gauge* g, uint64_t seed, uint64_t source_id, int t_first, int n_t, int prec,
                          void* out, cudaStream_t s);

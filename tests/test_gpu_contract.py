@@ -53,17 +53,21 @@ def test_contraction_matches_oracle(ctx, dims, t_bc, prec):
     g.close()
 
 
-@pytest.mark.parametrize("dims,prec", [((24, 20, 2, 2), abi.TSM_F32), ((24, 20, 2, 2), abi.TSM_F64),
-                                       ((40, 40, 2, 2), abi.TSM_F64)])
-def test_contraction_large_planes_radius_8(ctx, dims, prec):
-    """Planes large enough, with momentum components up to 8, that the x/y
-    transform takes 4, 2 or a single field per block instead of 8 (its
-    shared memory per block grows with the plane and the radius)."""
+@pytest.mark.parametrize("dims,prec,radius", [((40, 32, 2, 2), abi.TSM_F32, 3), ((24, 20, 2, 2), abi.TSM_F64, 8),
+                                              ((40, 40, 2, 2), abi.TSM_F64, 8)])
+def test_contraction_large_planes(ctx, dims, prec, radius):
+    """Planes large enough that the x/y transform takes 4 (FP32, the
+    p^2 <= 9 momenta), 2 or a single field (FP64, components up to 8) per
+    block instead of 8: its shared memory per block grows with the plane and
+    the momentum radius."""
     kappa, mu = 0.125, 0.01
     g, links = gauge(ctx, dims, 0.3, 6, -1)
     u = lattice.effective_links(links, -1)
     s = round_to(synth.gaussian_spinor(dims, 42, nrhs=2), prec)
-    moms = [(0, 0, 0), (8, 0, 0), (0, -8, 1), (3, 5, -8), (-7, 2, 4), (1, 1, 1)]
+    if radius == 3:
+        moms = momenta.momentum_list(9)
+    else:
+        moms = [(0, 0, 0), (8, 0, 0), (0, -8, 1), (3, 5, -8), (-7, 2, 4), (1, 1, 1)]
     nat = g.pack(to_device(s), prec)
     out = api.loops_complex(g.contract(kappa, mu, prec, nat, 2, moms))
     want = _oracle_loops(u, s, kappa, mu, dims, moms)
