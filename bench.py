@@ -397,8 +397,9 @@ def _dslash_roofline(g, abi, torch, peak, prec, nrhs, reps=10):
 
 def measured_traffic(kernel_class):
     """DRAM bytes per launch of `kernel_class` from the committed ncu capture
-    (profiles/roofline_traffic.txt), or None when that capture was taken on
-    different CUDA sources or for another kernel."""
+    (profiles/roofline_traffic.txt), or None when that capture was taken for
+    another kernel or on other sources of the kernel's translation unit (the
+    record's source_files; all CUDA sources when it lists none)."""
     from paper_1401_6750_gb300 import build
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "roofline_traffic.txt")
     try:
@@ -406,7 +407,7 @@ def measured_traffic(kernel_class):
             rec = json.load(fh)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_class") != kernel_class or rec.get("source_digest") != build.source_digest():
+    if rec.get("kernel_class") != kernel_class or rec.get("source_digest") != build.source_digest(rec.get("source_files")):
         return None
     return rec.get("dram_bytes_per_launch")
 

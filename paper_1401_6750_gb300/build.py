@@ -50,15 +50,31 @@ def _digest(extra_flags):
     return h.hexdigest()
 
 
-def source_digest():
-    """sha256 of the CUDA sources and public headers (names and contents): a
-    profile taken on one tree is valid for another only if this matches."""
+def source_digest(names=None):
+    """sha256 of CUDA sources and public headers (names and contents): a
+    profile taken on one tree is valid for another only if this matches.
+    names: the basenames a kernel's translation unit is compiled from (the
+    digest then also covers the compiler flags but not the checkout's include
+    paths); None: every source."""
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    if names is None:
+        files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    else:
+        files = []
+        for n in sorted(names):
+            cand = [os.path.join(d, n) for d in (CSRC, INCLUDE) if os.path.exists(os.path.join(d, n))]
+            files.append(cand[0] if cand else n)
     for f in files:
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        if os.path.exists(f):
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        else:
+            h.update(b"<missing>")
+    if names is not None:  # the flags, without the include paths (which differ between checkouts)
+        flags = ARCH + FLAGS
+        kept = [f for k, f in enumerate(flags) if f != "-I" and not (k > 0 and flags[k - 1] == "-I")]
+        h.update(" ".join(kept).encode())
     return h.hexdigest()
 
 

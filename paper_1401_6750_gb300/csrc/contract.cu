@@ -658,17 +658,22 @@ __global__ void __launch_bounds__(Z_BS) project_z_kernel(const PT* __restrict__ 
   const int nx = 2 * rad + 1, nxy = nx * nx;
   cplx<Z>* twz = reinterpret_cast<cplx<Z>*>(smem_raw);  // [nx][lz]: e^{-2 pi i n z / Lz}
   cplx<Z>* shf = twz + (size_t)nx * lz;                   // [nx]: 1 + e^{-2 pi i n / L_mu}, mu = pass - 1
-  for (int q = threadIdx.x; q < nx * lz + nx; q += blockDim.x) {
+  cplx<Z>* root = shf + nx;                               // [lz]: e^{-2 pi i m / Lz}
+  for (int q = threadIdx.x; q < lz + nx; q += blockDim.x) {  // the Lz + nx distinct phases, in FP64
     double sn, cs;
-    if (q < nx * lz) {
-      const int n = q / lz - rad, zz = q % lz;
-      sincospi(2.0 * (double)(((n * zz) % lz + lz) % lz) / (double)lz, &sn, &cs);
-      twz[q] = mk<Z>(Z(cs), Z(-sn));
+    if (q < lz) {
+      sincospi(2.0 * (double)q / (double)lz, &sn, &cs);
+      root[q] = mk<Z>(Z(cs), Z(-sn));
     } else if (pass >= 1 && pass <= 3) {
-      const int n = q - nx * lz - rad, L = g.L[pass - 1];
+      const int n = q - lz - rad, L = g.L[pass - 1];
       sincospi(2.0 * (double)(((n % L) + L) % L) / (double)L, &sn, &cs);
       shf[n + rad] = mk<Z>(Z(1.0 + cs), Z(-sn));
     }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nx * lz; q += blockDim.x) {
+    const int n = q / lz - rad, zz = q % lz;
+    twz[q] = root[((n * zz) % lz + lz) % lz];
   }
   __syncthreads();
   const int field0 = pass * NF + k * 16;
@@ -712,7 +717,7 @@ int launch_z(const tsm_gauge* g, const void* part, const int* mom_dev, int n_mom
   using PT = typename PartOf<R>::type;
   using Z = typename ZReal<PT>::type;
   const int lz = g->geom.L[2], lt = g->geom.L[3], nx = 2 * rad + 1;
-  const size_t zsmem = ((size_t)nx * lz + nx) * sizeof(cplx<Z>);
+  const size_t zsmem = ((size_t)nx * lz + nx + lz) * sizeof(cplx<Z>);
   TSM_CUDA(cudaFuncSetAttribute(project_z_kernel<PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zsmem));
   count_launches(1);
   project_z_kernel<PT><<<z_grid(lt, n_mom), Z_BS, zsmem, st>>>(static_cast<const PT*>(part), mom_dev, n_mom, g->geom,

@@ -2,6 +2,8 @@
 // and conversions between the plain and the chunked spinor layouts.
 #include <math.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace tsm {
@@ -123,8 +125,10 @@ __global__ void z4_kernel(uint64_t seed, uint64_t first, int V, void* out, int t
 
 // The same Z4 sources split by parity for the even-odd solvers: site i of
 // field r goes to odd or even at i >> 1 (all extents even), and the even
-// sites also to diag_even as (cr + i ci g5) eta_e (M_ee^{-1} eta_e), in the
-// arithmetic of the element-wise kernels.
+// sites also to diag_even as (cr + i ci g5) eta_e (M_ee^{-1} eta_e).  Every
+// component of that product is exactly +-cr or +-ci, so float-float fields
+// are computed in float-float (no FP64 work), the others in their own
+// element-wise arithmetic.
 template <int P>
 __global__ void z4_eo_kernel(uint64_t seed, uint64_t first, Geom g, void* even, void* odd, void* diag_even, double cr,
                              double ci) {
@@ -134,12 +138,12 @@ __global__ void z4_eo_kernel(uint64_t seed, uint64_t first, Geom g, void* even, 
   uint64_t x[4] = {(uint64_t)i, 0ull, 0ull, 0ull};
   philox4x64_10(x, seed, first + (uint64_t)r);
   const uint64_t w = x[0];
-  using R = ew_real<P>;
+  using R = typename std::conditional<P == TSM_DS, dsf, ew_real<P>>::type;
   cplx<R> v[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     const int z = (int)((w >> (2 * k)) & 3ull);
-    v[k] = mk<R>((R)(z == 0 ? 1 : (z == 2 ? -1 : 0)), (R)(z == 1 ? 1 : (z == 3 ? -1 : 0)));
+    v[k] = mk<R>(R(z == 0 ? 1 : (z == 2 ? -1 : 0)), R(z == 1 ? 1 : (z == 3 ? -1 : 0)));
   }
   int c[4];
   site_coords(g, i, c);
@@ -149,7 +153,7 @@ __global__ void z4_eo_kernel(uint64_t seed, uint64_t first, Geom g, void* even, 
     return;
   }
   SpinorIO<P>::store(even, vh, r, i >> 1, v);
-  const R a = (R)cr, b = (R)ci;
+  const R a = R(cr), b = R(ci);
 #pragma unroll
   for (int k = 0; k < 12; ++k) v[k] = a * v[k] + (k < 6 ? b : -b) * times_i(v[k]);
   SpinorIO<P>::store(diag_even, vh, r, i >> 1, v);

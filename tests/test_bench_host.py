@@ -1,4 +1,5 @@
-"""Host logic of bench.py that needs no GPU: the clock sampler.
+"""Host logic of bench.py that needs no GPU: the clock sampler, and the
+lookup of the committed traffic capture (end of file).
 
 A stand-in `nvidia-smi` on PATH prints the queried fields every 50 ms (first
 clocks at 2070 MHz with no throttle reason, then 1500 MHz with sw_power_cap
@@ -71,3 +72,35 @@ def test_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     c = bench.ClockSampler(0)
     c.start()
     assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_record_keyed_to_its_sources(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed capture only while the files
+    of the captured kernel's translation unit are those it was taken on: an
+    edit to another source keeps it, an edit to a listed file voids it."""
+    import json
+    import shutil
+    import bench
+    from paper_1401_6750_gb300 import build
+    files = ["eo.cu", "dslash.cuh", "common.cuh", "tsm.h"]
+    here = build.source_digest(files)
+    csrc, inc = tmp_path / "csrc", tmp_path / "include"
+    shutil.copytree(build.CSRC, csrc)
+    shutil.copytree(build.INCLUDE, inc)
+    monkeypatch.setattr(build, "CSRC", str(csrc))
+    monkeypatch.setattr(build, "INCLUDE", str(inc))
+    assert build.source_digest(files) == here  # another checkout of the same files
+    rec = {"kernel_class": "k", "dram_bytes_per_launch": 1234, "source_files": files,
+           "source_digest": build.source_digest(files)}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "roofline_traffic.txt").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "__file__", str(tmp_path / "bench.py"))
+    assert bench.measured_traffic("k") == 1234
+    assert bench.measured_traffic("other") is None
+    with open(csrc / "contract.cu", "a") as fh:  # not part of the kernel's unit
+        fh.write("\n// edit\n")
+    assert bench.measured_traffic("k") == 1234
+    with open(csrc / "dslash.cuh", "a") as fh:
+        fh.write("\n// edit\n")
+    assert bench.measured_traffic("k") is None
