@@ -316,7 +316,7 @@ int tsm_contract_hpe(tsm_gauge* g, double kappa, double mu, int prec,
  * array of TSM_CONTRACT_NOALLOC_MAX_BYTES compiled into the library, which
  * every GPU that loads the library holds until the process exits.  Needs
  *   256-rounded(12 n_mom) + 256-rounded(nsrc * V * 16 * NCH)
- *   + 256-rounded(160 * V * c) + 256-rounded(Lz * T * 160 * (2R+1)^2 * 16)
+ *   + 256-rounded(160 * V * c) + 256-rounded(Lz * T * 160 * (2R+1)^2 * c)
  *   bytes (R = max |n_i|; c = 8 for F32 solutions, 16 for F64)
  * and returns TSM_ERR_INVALID_ARG, touching nothing, when that exceeds the
  * maximum.  The first call on a device looks up the array's device address

@@ -1330,7 +1330,7 @@ int contract_loops_noalloc(tsm_gauge* g, double kappa, double mu, int prec, cons
   const size_t mom_bytes = round256(sizeof(int) * 3 * (size_t)n_mom);
   const size_t v_bytes = round256((size_t)nsrc * spinor_chunks(prec) * V * 16);
   const size_t f_bytes = round256((size_t)160 * V * cs);
-  const size_t part_bytes = round256((size_t)lz * lt * 160 * nx * nx * sizeof(double2));
+  const size_t part_bytes = round256((size_t)lz * lt * 160 * nx * nx * cs);  // float2 / double2 partials
   const size_t need = mom_bytes + v_bytes + f_bytes + part_bytes;
   if (need > (size_t)TSM_CONTRACT_NOALLOC_MAX_BYTES)
     return fail(TSM_ERR_INVALID_ARG,

@@ -67,7 +67,7 @@ def test_noalloc_matches_regular_entry_two_calls(ctx, prec, tol):
 
 
 def test_noalloc_rejects_oversize_request(ctx):
-    dims = (16, 16, 16, 32)  # partial sums for |n_i| <= 3 alone need 64 MiB
+    dims = (16, 16, 16, 32)  # the 160 FP32 site fields alone need 160 MiB
     g, _ = gauge(ctx, dims, 0.3, 8, -1, precs=(abi.TSM_F32,))
     lib = abi.lib()
     nat = g.empty_native(abi.TSM_F32, 1)
