@@ -27,14 +27,16 @@ namespace tsm {
 
 namespace {
 
+// out = bulk / N_LP + (hp - lpc) / N_HP; *bad is set when a value is not finite
 __global__ void combine_kernel(const double* __restrict__ bulk, const double* __restrict__ hp,
                                const double* __restrict__ lpc, double inv_lp, double inv_hp, size_t n,
-                               double* __restrict__ out) {
+                               double* __restrict__ out, int* __restrict__ bad) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double e = bulk[i] * inv_lp;
   if (inv_hp != 0.0) e += (hp[i] - lpc[i]) * inv_hp;
   out[i] = e;
+  if (!isfinite(e)) *bad = 1;
 }
 
 struct Accum {
@@ -153,12 +155,14 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
   const int batch = p->nrhs_per_launch > 0 ? std::min(p->nrhs_per_launch, 1024) : 12;
   const size_t n_out = (size_t)160 * p->n_mom * g->geom.L[3] * 2;
   std::lock_guard<std::mutex> lock(g->tsm_mu);
-  TSM_TRY(g->tsm_acc.reserve(sizeof(double) * n_out * 4));
+  TSM_TRY(g->tsm_acc.reserve(sizeof(double) * n_out * 4 + 16));
   double* bulk = g->tsm_acc.as<double>();
   double* hp = bulk + n_out;
   double* lpc = hp + n_out;
   double* est = est_dev ? est_dev : lpc + n_out;
+  int* bad = reinterpret_cast<int*>(lpc + 2 * n_out);  // non-finite flag of the estimate
   TSM_CUDA(cudaMemsetAsync(bulk, 0, sizeof(double) * n_out * 3, s));
+  TSM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
   Accum lp_a, hp_a, lpc_a;
   const uint64_t c0 = (uint64_t)p->n_lp;
   if (p->n_hp == 0 || !concurrent_correction()) {
@@ -216,11 +220,13 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
   const int bs = 256;
   count_launches(1);
   combine_kernel<<<(unsigned)((n_out + bs - 1) / bs), bs, 0, s>>>(bulk, hp, lpc, 1.0 / p->n_lp,
-                                                                  p->n_hp ? 1.0 / p->n_hp : 0.0, n_out, est);
+                                                                  p->n_hp ? 1.0 / p->n_hp : 0.0, n_out, est, bad);
   TSM_CUDA(cudaGetLastError());
   if (parts_dev) TSM_CUDA(cudaMemcpyAsync(parts_dev, bulk, sizeof(double) * n_out * 3, cudaMemcpyDeviceToDevice, s));
   if (loops_host) TSM_CUDA(cudaMemcpyAsync(loops_host, est, sizeof(double) * n_out, cudaMemcpyDeviceToHost, s));
   if (parts_host) TSM_CUDA(cudaMemcpyAsync(parts_host, bulk, sizeof(double) * n_out * 3, cudaMemcpyDeviceToHost, s));
+  int bad_host = 0;
+  if (loops_host) TSM_CUDA(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   if (loops_host || parts_host || stats) TSM_CUDA(cudaStreamSynchronize(s));
   if (stats) {
     memset(stats, 0, sizeof(*stats));
@@ -233,9 +239,7 @@ static int run_tsm(tsm_gauge* g, const tsm_params* p, double* est_dev, double* p
     stats->n_not_converged = lp_a.not_conv + hp_a.not_conv;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
-  if (loops_host)
-    for (size_t k = 0; k < n_out; ++k)
-      if (!isfinite(loops_host[k])) return fail(TSM_ERR_NONFINITE, "non-finite loop value");
+  if (loops_host && bad_host) return fail(TSM_ERR_NONFINITE, "non-finite loop value");
   if (lp_a.not_conv + hp_a.not_conv)
     return fail(TSM_ERR_NOT_CONVERGED, "%d solves missed rho", lp_a.not_conv + hp_a.not_conv);
   return TSM_OK;
