@@ -321,7 +321,9 @@ int tsm_contract_hpe(tsm_gauge* g, double kappa, double mu, int prec,
  * and returns TSM_ERR_INVALID_ARG, touching nothing, when that exceeds the
  * maximum.  The first call on a device looks up the array's device address
  * and uploads a constant table there (make it before any stream capture);
- * no call allocates device memory.  That address is kept for the life of the
+ * no call allocates device memory.  Every call copies the momentum list from
+ * the caller's host array, so calls inside a stream capture are not
+ * supported (a graph would re-read that host array at each replay).  That address is kept for the life of the
  * process: a cudaDeviceReset after the first call is not supported.  All calls share the array and it keeps
  * the last call's contents: calls that overlap on the GPU (two streams, two
  * threads) race.  Results equal tsm_contract_loops'. */
