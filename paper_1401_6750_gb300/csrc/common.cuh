@@ -192,6 +192,23 @@ __device__ __forceinline__ int fwd_site(const Geom& g, int i, const int c[4], in
 __device__ __forceinline__ int bwd_site(const Geom& g, int i, const int c[4], int mu, int stride) {
   return (c[mu] == 0) ? i + (g.L[mu] - 1) * stride : i - stride;
 }
+// Forward neighbour for a direction known only at run time, written with
+// selects: an array or kernel-parameter field indexed at run time is copied
+// to local memory by the compiler (a per-thread stack frame).
+__device__ __forceinline__ int fwd_site_rt(const Geom& g, int i, const int c[4], int mu) {
+  const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+  const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+  const int lm = mu == 0 ? L0 : (mu == 1 ? L1 : (mu == 2 ? L2 : L3));
+  const int st = mu == 0 ? 1 : (mu == 1 ? L0 : (mu == 2 ? L0 * L1 : L0 * L1 * L2));
+  return cm == lm - 1 ? i - (lm - 1) * st : i + st;
+}
+__device__ __forceinline__ int bwd_site_rt(const Geom& g, int i, const int c[4], int mu) {
+  const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+  const int cm = mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+  const int lm = mu == 0 ? L0 : (mu == 1 ? L1 : (mu == 2 ? L2 : L3));
+  const int st = mu == 0 ? 1 : (mu == 1 ? L0 : (mu == 2 ? L0 * L1 : L0 * L1 * L2));
+  return cm == 0 ? i + (lm - 1) * st : i - st;
+}
 
 // ---------------------------------------------------------------- spinor IO
 // Chunked layout: chunk j of site i of field r at ((r*NCH + j)*V + i)*16 bytes.

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) contract_field
     const int mu = pass - 1;
     int c[4];
     site_coords(a.g, i, c);
-    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    const int nf = fwd_site_rt(a.g, i, c, mu);
     cplx<R> u[3][3];
     LinkIO<PL>::load(a.links, V, mu, i, u);
     const R sf = (mu == 3 && c[3] == a.g.L[3] - 1) ? (R)a.g.bc : (R)1;
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(FLD_BS, 3) contract_fields_pairs_kernel(FieldA
     const int mu = pass - 1;
     int c[4];
     site_coords(a.g, i, c);
-    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    const int nf = fwd_site_rt(a.g, i, c, mu);
     cplx<float> u[3][3];
     LinkIO<PL>::load(a.links, V, mu, i, u);
     if (mu == 3 && c[3] == a.g.L[3] - 1 && a.g.bc < 0) {  // boundary sign folded into the link
@@ -785,7 +785,7 @@ __global__ void __launch_bounds__(FLD_BS, sizeof(R) == 4 ? 3 : 1) tdil_fields_ke
     }
   } else {
     const int mu = pass - 1;
-    const int nf = fwd_site(a.g, i, c, mu, dir_stride(a.g, mu));
+    const int nf = fwd_site_rt(a.g, i, c, mu);
     const int tn = (mu == 3) ? (c[3] + 1 == a.g.L[3] ? 0 : c[3] + 1) : c[3];
     cplx<R> u[3][3];
     LinkIO<PL>::load(a.links, V, mu, i, u);

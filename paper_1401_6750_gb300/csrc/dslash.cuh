@@ -353,8 +353,7 @@ __device__ __forceinline__ void stencil_rolled(cplx<R> (&acc)[NR][12], const Dsl
     const int mu = hop >> 1;
     const bool back = (hop & 1) != 0;
     const int S = back ? -SF : SF;  // projector sign of this hop
-    const int stride = dir_stride(a.g, mu);
-    const int n = back ? bwd_site(a.g, i, c, mu, stride) : fwd_site(a.g, i, c, mu, stride);
+    const int n = back ? bwd_site_rt(a.g, i, c, mu) : fwd_site_rt(a.g, i, c, mu);
     cplx<R> u[3][3];
     LinkIO<PL>::load(a.links, V, mu, back ? n : i, u);
     if (back) {  // U^dag in place
@@ -387,9 +386,10 @@ __device__ __forceinline__ void stencil_rolled(cplx<R> (&acc)[NR][12], const Dsl
       SpinorIO<PIN>::load(a.in, FS, r0 + q, EO ? (n >> 1) : n, p);
       cplx<R> h0[3], h1[3];
 #pragma unroll
-      for (int col = 0; col < 3; ++col) {
-        h0[col] = p[col] + unit_times(p[3 * j0 + col], rot, neg0);
-        h1[col] = p[3 + col] + unit_times(p[3 * j1 + col], rot, neg1);
+      for (int col = 0; col < 3; ++col) {  // spins j0, j1 selected, not indexed (p stays in registers)
+        const cplx<R> pj0 = j0 == 3 ? p[9 + col] : p[6 + col], pj1 = j1 == 3 ? p[9 + col] : p[6 + col];
+        h0[col] = p[col] + unit_times(pj0, rot, neg0);
+        h1[col] = p[3 + col] + unit_times(pj1, rot, neg1);
       }
       cplx<R> w0[3], w1[3];
 #pragma unroll
