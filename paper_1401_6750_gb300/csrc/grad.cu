@@ -153,7 +153,10 @@ __global__ void __launch_bounds__(G_BS) weights_kernel(Geom geo, const double* _
           const int b = c_gamma_grad.col[gi][a];
           const R gr = (R)c_gamma_grad.re[gi][a], gim = (R)c_gamma_grad.im[gi][a];
           const R sgn = a < 2 ? (R)1 : (R)-1;
-          om[4 * a + b] = om[4 * a + b] + sgn * cmul(mk<R>(gr, gim), w[gi]);
+          const cplx<R> v = sgn * cmul(mk<R>(gr, gim), w[gi]);
+#pragma unroll
+          for (int bb = 0; bb < 4; ++bb)  // the column by comparison: om stays in registers
+            if (bb == b) om[4 * a + bb] = om[4 * a + bb] + v;
         }
     }
 #pragma unroll
@@ -345,15 +348,15 @@ __global__ void __launch_bounds__(G_BS) transpose_stencil_kernel(Geom geo, const
   SpinorIO<PS>::load(gs, V, r, i, accs);
   SpinorIO<PS>::load(gv, V, r, i, accv);
   for (int mu = 0; mu < 4; ++mu) {
-    const int stride = dir_stride(geo, mu);
-    const int nf = fwd_site(geo, i, c, mu, stride), nb = bwd_site(geo, i, c, mu, stride);
+    const int nf = fwd_site_rt(geo, i, c, mu), nb = bwd_site_rt(geo, i, c, mu);
     cplx<R> ub[3][3], uf[3][3];
     LinkIO<PL>::load(links, V, mu, nb, ub);  // U(y - mu)
     LinkIO<PL>::load(links, V, mu, i, uf);   // U(y)
     const R sb = (mu == 3 && c[3] == 0) ? (R)geo.bc : (R)1;
     const R sf = (mu == 3 && c[3] == geo.L[3] - 1) ? (R)geo.bc : (R)1;
     cplx<R> t[12], w[12];
-    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {  // unrolled: acc names one array, not a run-time choice
       cplx<R>(&acc)[12] = k == 0 ? accs : accv;
       SpinorIO<PS>::load(aw, V, 4 * k + mu, nb, t);
       cmatvec(w, ub, t, true, sb);
