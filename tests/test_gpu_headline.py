@@ -10,7 +10,11 @@ size rather than trusted from small lattices:
 * the FP32 contraction of that HP solution against the oracle's FP64
   densities and direct Fourier sums for a subset of insertions (scalar and
   g5 of both flavour structures, two derivative insertions), all 123
-  momenta, every timeslice: 1e-6 normwise per insertion.
+  momenta, every timeslice: 1e-6 normwise per insertion;
+* the standard-estimator contraction likewise;
+* the bench's TSM step itself: its LP-correction and HP sums against the
+  oracle's contraction of the regenerated correction vectors, and its
+  combination.
 """
 import numpy as np
 import pytest
@@ -89,3 +93,35 @@ def test_headline_standard_estimator_contraction(headline, t0):
     for k, ins in enumerate(sel):
         err = np.linalg.norm(got[ins] - want[k]) / np.linalg.norm(want[k])
         assert err < 1e-6, (t0, ins, err)
+
+
+def test_headline_tsm_step_correction_sums(headline):
+    """The bench's TSM step itself (32 FP16 LP + 2 HP sources, 32 right-hand
+    sides per launch, even-odd maps, the correction chain on its own stream):
+    the driver's LP-correction and HP sums equal the oracle's FP64 contraction
+    of the two correction sources' LP and HP vectors, regenerated source by
+    source (one map per source, whatever the batch), on the six insertions
+    above and all 123 momenta (1e-6); the estimate is the combination of the
+    driver's three sums."""
+    g, u = headline
+    moms = momenta.momentum_list(9)
+    lp, hp = abi.TSM_SOLVER_LP_F16 | EO, abi.TSM_SOLVER_F32_RELIABLE | EO
+    n_lp, n_hp = 32, 2
+    est, parts, st = g.tsm(KAPPA, MU, n_lp, n_hp, 1e-2, 1e-8, lp, hp, SEED, moms, nrhs_per_launch=32,
+                           want_parts=True)
+    assert st["n_not_converged"] == 0
+    comb = parts[0] / n_lp + (parts[1] - parts[2]) / n_hp
+    assert np.abs(est - comb).max() <= 1e-12 * np.abs(est).max()
+    lp_nat, _ = g.solve_sources(KAPPA, MU, lp, 1e-2, SEED, n_lp, n_hp, nrhs_per_launch=32)
+    hp_nat, _ = g.solve_sources(KAPPA, MU, hp, 1e-8, SEED, n_lp, n_hp, nrhs_per_launch=32)
+    x_lp = g.unpack(lp_nat, abi.TSM_F32, n_hp).cpu().numpy()
+    # the driver contracts HP solutions in FP32
+    x_hp = g.unpack(g.pack(g.unpack(hp_nat, abi.TSM_F64, n_hp), abi.TSM_F32), abi.TSM_F32, n_hp).cpu().numpy()
+    sel = [0, 15, 80, 95,
+           contract.insertion_index(0, True, 0, 1), contract.insertion_index(1, True, 3, 8)]
+    for which, x in ((2, x_lp), (1, x_hp)):
+        want = sum(contract.project(contract.loop_densities(u, x[r], KAPPA, MU, only=set(sel))[sel], DIMS, moms)
+                   for r in range(n_hp))
+        for k, ins in enumerate(sel):
+            err = np.linalg.norm(parts[which][ins] - want[k]) / np.linalg.norm(want[k])
+            assert err < 1e-6, (which, ins, err)
